@@ -1,0 +1,369 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix (no GPU).
+
+Each test checks the oracle against something other than itself: brute-force enumeration
+of every substring / every alignment on tiny inputs, closed forms printed in the paper,
+invariants of the maximum scoring subsequence, and the paper's Figure 2 toy genome.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+ALPHA = "ACGTN"
+COMP = {"A": "T", "C": "G", "G": "C", "T": "A", "N": "N"}
+
+
+def revcomp(s: str) -> str:
+    return "".join(COMP[c] for c in reversed(s))
+
+
+def sub_score(a: str, b: str, match: int, mismatch: int) -> int:
+    return match if (a == b and a != "N") else mismatch
+
+
+# ---------------------------------------------------------------- maximum scoring subsequence
+def brute_mss(x):
+    """max over all contiguous runs x[i:j] (empty run allowed) — "Maximum scoring subsequence"."""
+    best = 0
+    for i in range(len(x) + 1):
+        for j in range(i, len(x) + 1):
+            best = max(best, sum(x[i:j]))
+    return best
+
+
+def test_mss_bruteforce():
+    rng = np.random.default_rng(1)
+    for _ in range(400):
+        n = int(rng.integers(0, 14))
+        x = rng.integers(-6, 7, size=n).tolist()
+        assert oracle.mss(x) == brute_mss(x)
+
+
+def test_mss_special_cases():
+    assert oracle.mss([]) == 0                      # empty sequence: empty run
+    assert oracle.mss([-3, -1, -7]) == 0            # all negative: empty run wins
+    assert oracle.mss([2, 3, 4]) == 9               # all positive: whole sequence
+    assert oracle.mss([5, -10, 4, 4]) == 8          # a dip resets the run
+    assert oracle.mss([5, -1, 4]) == 8              # a small dip is bridged
+
+
+# ---------------------------------------------------------------- one diagonal, tiny inputs
+def brute_diag(read: str, gpad: str, d: int, match: int, mismatch: int) -> int:
+    x = [sub_score(read[k], gpad[d + k], match, mismatch) for k in range(len(read))]
+    return brute_mss(x)
+
+
+@pytest.mark.parametrize("match,mismatch", [(1, -1), (5, -4), (3, 0), (2, -7)])
+def test_diag_score_bruteforce(match, mismatch):
+    rng = np.random.default_rng(2 + match)
+    for _ in range(60):
+        G = int(rng.integers(1, 40))
+        m = int(rng.integers(1, 12))
+        genome = "".join(rng.choice(list(ALPHA), p=[.22, .22, .22, .22, .12], size=G))
+        read = "".join(rng.choice(list(ALPHA), p=[.23, .23, .23, .23, .08], size=m))
+        gpad = genome + "N" * m
+        q = oracle.encode(read)
+        g = oracle.encode(gpad)
+        for d in range(G):
+            assert oracle.diag_score(q, g, d, match, mismatch) == brute_diag(read, gpad, d, match, mismatch)
+
+
+# ---------------------------------------------------------------- whole phase one, tiny inputs
+def brute_map(genome: str, F: int, read: str, match: int, mismatch: int):
+    """Phase one by enumeration: every strand, every diagonal of every fragment, every
+    substring; fragment maximum with its first (strand, d); top two by sorting."""
+    G = len(genome)
+    NF = -(-G // F)
+    Gp = NF * F
+    m = len(read)
+    gpad = genome + "N" * (Gp - G + m)
+    reads = [read, revcomp(read)]
+    frag = []
+    for f in range(NF):
+        cands = []
+        for sg in range(2):
+            for d in range(f * F, (f + 1) * F):
+                cands.append((brute_diag(reads[sg], gpad, d, match, mismatch), sg, d))
+        best = max(c[0] for c in cands)
+        first = min((sg, d) for (s, sg, d) in cands if s == best)
+        frag.append((best, first[0], first[1]))
+    order = sorted(range(NF), key=lambda f: (-frag[f][0], f))
+    b1 = order[0]
+    b2 = order[1] if NF > 1 else -1
+    s1 = frag[b1][0]
+    s2 = frag[b2][0] if b2 >= 0 else 0
+    repeat = 1 if (s1 == 0 or s2 / s1 >= 0.9) else 0
+    return (b1, b2, s1, s2, frag[b1][2], frag[b1][1], repeat), [f[0] for f in frag]
+
+
+@pytest.mark.parametrize("F", [1, 3, 5, 8, 16])
+def test_map_read_bruteforce(F):
+    rng = np.random.default_rng(10 + F)
+    for trial in range(25):
+        G = int(rng.integers(1, 48))
+        m = int(rng.integers(1, 10))
+        genome = "".join(rng.choice(list(ALPHA), p=[.23, .23, .23, .23, .08], size=G))
+        if trial % 3 == 0 and G >= m:   # plant a (possibly reversed) copy so that ties and repeats occur
+            s = int(rng.integers(0, G - m + 1))
+            read = genome[s:s + m]
+            if trial % 2:
+                read = revcomp(read)
+        else:
+            read = "".join(rng.choice(list(ALPHA), p=[.24, .24, .24, .24, .04], size=m))
+        match, mismatch = [(1, -1), (5, -4), (2, -3)][trial % 3]
+        want, wfs = brute_map(genome, F, read, match, mismatch)
+        got, fs = oracle.map_read(genome, F, read, match, mismatch, with_frag_scores=True)
+        assert got == want, (genome, F, read)
+        assert fs.tolist() == wfs
+
+
+# ---------------------------------------------------------------- invariants
+def test_exact_substring_scores_m_match():
+    rng = np.random.default_rng(3)
+    genome = "".join(rng.choice(list("ACGT"), size=3000))
+    for m, d in [(50, 17), (100, 1234), (31, 2969)]:
+        read = genome[d:d + m]
+        hit = oracle.map_read(genome, 256, read, 5, -4)
+        assert hit[2] == m * 5
+        assert hit[4] == d and hit[5] == 0
+        assert hit[0] == d // 256
+        rc = oracle.map_read(genome, 256, revcomp(read), 5, -4)
+        assert rc[2] == m * 5 and rc[4] == d and rc[5] == 1
+
+
+def test_all_mismatch_diagonal_scores_zero():
+    q = oracle.encode("A" * 20)
+    g = oracle.encode("C" * 40)
+    assert oracle.diag_score(q, g, 3, 5, -4) == 0
+    hit = oracle.map_read("CG" * 45, 16, "A" * 12, 5, -4)   # reverse strand is T*12: no match either
+    assert hit[2] == 0 and hit[3] == 0 and hit[6] == 1   # best == 0 -> unmapped
+
+
+def test_fragment_score_is_max_over_its_diagonals():
+    rng = np.random.default_rng(4)
+    genome = "".join(rng.choice(list("ACGT"), size=500))
+    read = "".join(rng.choice(list("ACGT"), size=40))
+    F = 64
+    hit, fs = oracle.map_read(genome, F, read, 1, -1, with_frag_scores=True)
+    gpad = oracle.encode(genome + "N" * (len(fs) * F - len(genome) + 40))
+    q = [oracle.encode(read), oracle.encode(revcomp(read))]
+    for f in range(len(fs)):
+        best = max(oracle.diag_score(q[s], gpad, d, 1, -1) for s in range(2) for d in range(f * F, (f + 1) * F))
+        assert fs[f] == best
+    assert hit[2] == max(fs)
+
+
+def test_reverse_complement_symmetry():
+    rng = np.random.default_rng(5)
+    genome = "".join(rng.choice(list("ACGT"), size=2000))
+    for d in (0, 333, 1900):
+        read = list(genome[d:d + 60])
+        for p in rng.choice(60, size=6, replace=False):   # a few substitutions keep it unique
+            read[p] = {"A": "C", "C": "G", "G": "T", "T": "A"}[read[p]]
+        read = "".join(read)
+        a = oracle.map_read(genome, 100, read, 5, -4)
+        b = oracle.map_read(genome, 100, revcomp(read), 5, -4)
+        assert a[:5] == b[:5] and a[5] == 1 - b[5]
+
+
+def test_junction_alignment_is_not_lost():
+    """A read planted across a fragment border scores m*match in the fragment holding its
+    start diagonal (windows run into the right neighbour: "First phase", Figure 1)."""
+    rng = np.random.default_rng(6)
+    genome = "".join(rng.choice(list("ACGT"), size=4000))
+    F = 1000
+    d = 2 * F - 30
+    read = genome[d:d + 100]
+    hit = oracle.map_read(genome, F, read, 1, -1)
+    assert hit[0] == 1 and hit[2] == 100 and hit[4] == d
+
+
+def test_planted_repeat_ties_go_to_lowest_fragment():
+    rng = np.random.default_rng(7)
+    genome = list(rng.choice(list("ACGT"), size=5000))
+    src = 3100
+    genome[700:900] = genome[src:src + 200]      # exact copy, earlier fragment
+    genome = "".join(genome)
+    read = genome[src + 20:src + 120]
+    hit = oracle.map_read(genome, 512, read, 5, -4)
+    assert hit[2] == hit[3] == 500
+    assert hit[0] == 720 // 512 and hit[1] == (src + 20) // 512
+    assert hit[6] == 1   # repeat
+
+
+def test_single_fragment_has_no_second():
+    hit = oracle.map_read("ACGTACGTAC", 64, "GTAC", 1, -1)
+    assert hit[0] == 0 and hit[1] == -1 and hit[3] == 0
+
+
+def test_ratio_flag_integer_form():
+    """Mapped iff second/best < 0.9 ("First phase of MaxSSmap"); the oracle uses the exact
+    integer form 10*second >= 9*best."""
+    rng = np.random.default_rng(8)
+    genome = "".join(rng.choice(list("ACGT"), size=1200))
+    for t in range(40):
+        read = "".join(rng.choice(list("ACGT"), size=int(rng.integers(8, 30))))
+        h = oracle.map_read(genome, 100, read, 1, -1)
+        b, s = h[2], h[3]
+        assert h[6] == (1 if (b == 0 or s / b >= 0.9) else 0)
+
+
+# ---------------------------------------------------------------- Figure 2 toy genome
+def _golden(name):
+    d = {}
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            k, *v = line.split()
+            d[k] = v
+    return d
+
+
+def test_figure2_toy_fragments():
+    g = _golden("fig2_toy.txt")
+    genome = g["genome"][0]
+    F = int(g["frag_len"][0])
+    frags = g["fragments"]
+    assert -(-len(genome) // F) == len(frags)
+    for f, s in enumerate(frags):
+        hit, fs = oracle.map_read(genome, F, s, 1, -1, with_frag_scores=True)
+        assert fs[f] == F          # the fragment's own bases score F*match in fragment f
+        assert hit[2] == F
+    # the transposed layout's first row is the first base of every fragment
+    assert "".join(genome[f * F] for f in range(len(frags))) == g["transposed_row0"][0]
+    # a read that starts in fragment 0 and runs into fragment 1 (junction) maps to fragment 0
+    hit = oracle.map_read(genome, F, genome[1:5], 1, -1)
+    assert hit[0] == 0 and hit[4] == 1 and hit[2] == 4
+
+
+# ---------------------------------------------------------------- closed forms printed in the paper
+def test_paper_closed_forms():
+    # MAPQ threshold: -100 log2 0.9 = 15.2 ("Mapping qualities")
+    assert round(-100 * math.log2(0.9), 1) == 15.2
+    # strict threshold 62 <-> ratio 2^-0.62 ~ 0.651 (ancient DNA section)
+    assert round(2 ** -0.62, 3) == 0.651
+    # maximum read length: profile (m+16)*4*5 bytes in 49152 bytes of shared memory -> 2441,
+    # largest multiple of 16 below it is 2432 ("Shared memory")
+    cap = 49152 / (4 * 5) - 16
+    assert int(cap) == 2441 and (int(cap) // 16) * 16 == 2432
+    # OpenMP thread counts "about 1042, 104 and 11" for fragment lengths 4800, 48000, 480000 on
+    # a ~5 Mbp genome: G/F rounded (the third, 10.4, is printed rounded up)
+    assert round(5e6 / 4800) == 1042 and round(5e6 / 48000) == 104 and math.ceil(5e6 / 480000) == 11
+
+
+# ---------------------------------------------------------------- phase two
+def alignment_score(read, window, ops, match, mismatch, go, ge):
+    i = j = 0
+    score = 0
+    prev = None
+    for op in ops:
+        if op == "M":
+            score += sub_score(read[i], window[j], match, mismatch)
+            i += 1
+            j += 1
+        elif op == "I":
+            score += ge if prev == "I" else go
+            i += 1
+        else:
+            score += ge if prev == "D" else go
+            j += 1
+        prev = op
+    return score, i, j
+
+
+def brute_glocal(read, window, match, mismatch, go, ge):
+    """Best glocal alignment by enumeration: every genome start, every op string."""
+    m, L = len(read), len(window)
+    best = None
+    for js in range(L + 1):
+        sub = window[js:]
+        # enumerate op strings with exactly m read-consuming ops and up to len(sub) genome ops
+        def rec(i, j, prev, score):
+            nonlocal best
+            if i == m:
+                if best is None or score > best:
+                    best = score
+                # trailing genome bases are free: stop here
+            if i < m and j < len(sub):
+                rec(i + 1, j + 1, "M", score + sub_score(read[i], sub[j], match, mismatch))
+            if i < m:
+                rec(i + 1, j, "I", score + (ge if prev == "I" else go))
+            if j < len(sub) and i < m:   # a deletion must be followed by more read (trailing ones are free)
+                rec(i, j + 1, "D", score + (ge if prev == "D" else go))
+        rec(0, 0, None, 0)
+    return best
+
+
+def parse_cigar(c):
+    ops, n = [], ""
+    for ch in c:
+        if ch.isdigit():
+            n += ch
+        else:
+            ops += [ch] * int(n)
+            n = ""
+    return ops
+
+
+def test_nw_bruteforce_tiny():
+    rng = np.random.default_rng(9)
+    for t in range(150):
+        m = int(rng.integers(1, 6))
+        L = int(rng.integers(0, 7))
+        window = "".join(rng.choice(list(ALPHA), p=[.24, .24, .24, .24, .04], size=L))
+        read = "".join(rng.choice(list(ALPHA), p=[.24, .24, .24, .24, .04], size=m))
+        match, mismatch, go, ge = [(5, -4, -26, -26), (5, -4, -10, -1), (2, -3, -4, -2), (1, -1, -2, -1)][t % 4]
+        want = brute_glocal(read, window, match, mismatch, go, ge)
+        got = oracle.nw_banded(oracle.encode(window) if L else np.zeros(0, np.uint8), oracle.encode(read), 0, 64,
+                               match, mismatch, go, ge) if L else None
+        if L == 0:
+            continue   # empty window: the oracle reports no alignment (no genome to anchor the read)
+        score, gs, ge_, cig = got
+        assert score == want, (read, window, match, mismatch, go, ge)
+        ops = parse_cigar(cig)
+        s2, i, j = alignment_score(read, window[gs:], ops, match, mismatch, go, ge)
+        assert s2 == score and i == m and gs + j == ge_
+
+
+def test_nw_hand_worked():
+    with open(os.path.join(GOLDEN, "nw_hand.txt")) as fh:
+        rows = [l.split() for l in fh if l.strip() and not l.startswith("#")]
+    for r in rows:
+        genome, read, d, W, ma, mm, go, ge, _, sc, cig, gs, gend = r
+        got = oracle.nw_banded(oracle.encode(genome), oracle.encode(read), int(d), int(W), int(ma), int(mm),
+                               int(go), int(ge))
+        assert got == (int(sc), int(gs), int(gend), cig), r
+
+
+def test_nw_banded_equals_unbanded_when_optimum_in_band():
+    rng = np.random.default_rng(11)
+    genome = "".join(rng.choice(list("ACGT"), size=3000))
+    g = oracle.encode(genome)
+    for t in range(20):
+        d = int(rng.integers(100, 2700))
+        read = list(genome[d:d + 120])
+        for p in rng.choice(120, size=12, replace=False):
+            read[p] = "ACGT"[(("ACGT".index(read[p])) + 1) % 4]
+        cut = int(rng.integers(20, 100))
+        k = int(rng.integers(1, 8))
+        read = read[:cut] + read[cut + k:] if t % 2 else read[:cut] + list("ACGT"[:k % 4 + 1]) + read[cut:]
+        q = oracle.encode("".join(read))
+        a = oracle.nw_banded(g, q, d, 32, 5, -4, -10, -1)
+        b = oracle.nw_banded(g, q, d, 400, 5, -4, -10, -1)
+        assert a == b
+
+
+def test_nw_literal_region():
+    """Literal reading: region starts at the best fragment and spans ceil(m/F) fragments."""
+    rng = np.random.default_rng(12)
+    genome = "".join(rng.choice(list("ACGT"), size=600))
+    F = 64
+    read = genome[130:170]   # inside fragment 2 (128..191)
+    sc, gs, ge, cig = oracle.nw_literal(oracle.encode(genome), F, 2, oracle.encode(read), 5, -4, -26, -26)
+    assert (sc, gs, ge, cig) == (200, 130, 170, "40M")
