@@ -1,0 +1,203 @@
+/*
+ * maxss.h — C ABI of libmaxss, a GB300 (sm_103a) implementation of the MaxSSmap hot path
+ * (Turki & Roshan, "MaxSSmap: A GPU program for mapping divergent short reads to genomes
+ * with the maximum scoring subsequence", arXiv 1403.2136).
+ *
+ * Phase one ("First phase of MaxSSmap"): for every read, on both strands, the maximum
+ * scoring subsequence (section "Maximum scoring subsequence": the best-sum contiguous run of
+ * match/mismatch scores, empty run allowed) along every ungapped diagonal d of the genome;
+ * fragment f (section "Coalescent global memory access": fixed-size disjoint fragments, the
+ * last one padded with N) owns diagonals [fF, (f+1)F) and its windows run into the next
+ * fragment (junctions, Figure 1); per read the best and second-best fragment, and the repeat
+ * test second/best >= 0.9.  Phase two ("Second phase of MaxSSmap"): Needleman-Wunsch of the
+ * read against the genome around the best diagonal.
+ *
+ * Conventions for every entry point:
+ *   - return MSS_OK (0) or a negative mss_status; mss_last_error() gives a message
+ *     (thread-local, valid until the next call on the same thread);
+ *   - no call aborts or exits the process, and nothing falls back to the CPU;
+ *   - the caller owns every input and output buffer; the context owns the packed genome and
+ *     its device workspaces;
+ *   - "stream" is a cudaStream_t passed as void* (NULL = the legacy default stream);
+ *   - *_device entry points take device pointers, enqueue work on the stream and return
+ *     without synchronising; errors found on the device are reported by mss_sync();
+ *     the other entry points take host pointers, copy in and out, and synchronise.
+ *   - base characters: A C G T N in either case; anything else is MSS_EINVAL.
+ */
+#ifndef MAXSS_H
+#define MAXSS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define MSS_API __attribute__((visibility("default")))
+#else
+#define MSS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t mss_status;
+
+#define MSS_OK 0
+#define MSS_EINVAL (-1)     /* bad argument, bad character, bad size */
+#define MSS_ENOMEM (-2)     /* device or host allocation failed */
+#define MSS_ECUDA (-3)      /* a CUDA runtime call failed */
+#define MSS_EREADLEN (-4)   /* read length 0 or above the context's maximum (at most 2432) */
+#define MSS_EOVERFLOW (-5)  /* max_read_len * match would overflow the 16-bit scan lanes */
+#define MSS_ETIMEOUT (-6)   /* a bounded device wait gave up */
+#define MSS_ESTATE (-7)     /* inconsistent internal state (a self-check failed) */
+
+/* Longest read accepted.  The paper's kernel holds a (m+16)x4x5-byte query profile in 48 KB
+   of shared memory, which caps m at 2432 ("Shared memory"); the cap is kept here as the
+   validity bound of the ABI. */
+#define MSS_MAX_READ_LEN 2432
+
+/* Score of an mss_aln for which no in-band alignment exists. */
+#define MSS_NW_NONE (-2147483647 - 1)
+
+typedef struct mss_ctx mss_ctx;
+
+typedef struct {
+  int64_t frag_len;     /* F: diagonals per fragment, 16 <= F <= 2^20 (0 = default 2048) */
+  int32_t max_read_len; /* longest read that will be mapped, 1..MSS_MAX_READ_LEN (0 = 2432) */
+  int32_t reserved;     /* must be 0 */
+} mss_genome_params;
+
+typedef struct {
+  int32_t match;    /* score of an identical A/C/G/T pair, 1..127 */
+  int32_t mismatch; /* score of any other pair (N never matches), -128..0 */
+} mss_score_params;
+
+/* Per-read result of phase one (32 bytes). */
+typedef struct {
+  int32_t best_frag;    /* fragment with the highest score; ties -> lowest index */
+  int32_t second_frag;  /* best among the other fragments (ties -> lowest), -1 if only one */
+  int32_t best_score;   /* S(best_frag) >= 0 */
+  int32_t second_score; /* S(second_frag), 0 if there is no second fragment */
+  int64_t offset;       /* diagonal d of best_frag attaining best_score: genome index of read
+                           base 0 on the chosen strand; ties -> + strand first, then smallest d */
+  int32_t strand;       /* 0: read as given, 1: reverse complement */
+  int32_t flags;        /* bit 0 (MSS_HIT_REPEAT): best == 0 or 10*second >= 9*best */
+} mss_hit;
+
+#define MSS_HIT_REPEAT 1
+
+typedef struct {
+  int32_t match;      /* default 5 ("Second phase of MaxSSmap") */
+  int32_t mismatch;   /* default -4 */
+  int32_t gap_open;   /* cost of the first base of a gap, default -26 (linear = open == extend) */
+  int32_t gap_extend; /* cost of each further base; require gap_open <= gap_extend <= 0 */
+  int32_t band;       /* W, 0..63: cells with |j - i - (d - window start)| <= W */
+  int32_t reserved;   /* must be 0 */
+} mss_nw_params;
+
+/* Per-read result of phase two (24 bytes). */
+typedef struct {
+  int32_t score;     /* alignment score, MSS_NW_NONE if no in-band alignment exists */
+  int32_t cigar_len; /* characters written (without the NUL); -1 if the slot was too small */
+  int64_t gstart;    /* genome index of the first aligned genome base */
+  int64_t gend;      /* one past the last aligned genome base */
+} mss_aln;
+
+typedef struct {
+  int64_t genome_len;   /* G */
+  int64_t frag_len;     /* F */
+  int64_t num_frags;    /* NF = ceil(G / F) */
+  int64_t padded_len;   /* Gp = NF * F */
+  int32_t max_read_len;
+  int32_t num_sms;
+} mss_genome_info;
+
+/* Scan configuration: chosen by mss_autotune() or set directly. */
+typedef struct {
+  int32_t variant;       /* 0: int16 DPX add-max-relu (any scores); 1: f16 add-relu on the FMA
+                            pipe + DPX running max (exact when max_read_len*match <= 2048 and the
+                            scores are small integers); -1 = pick automatically */
+  int32_t pairs;         /* diagonal pairs per thread: 4 or 8 (0 = default) */
+  int32_t queries;       /* query sequences (read strands) per CTA: 4 or 8 (0 = default) */
+  int32_t ctas_per_sm;   /* persistent CTAs per SM (0 = occupancy maximum) */
+  int32_t min_items_per_cta; /* split the genome into chunks until there are this many work
+                                items per CTA (0 = default 4) */
+  int32_t reserved;
+} mss_tune;
+
+/* Load and 2-bit pack a genome (host ASCII, length len >= 1).  Creates *out. */
+MSS_API mss_status mss_load_genome(mss_ctx** out, const char* seq, int64_t len, const mss_genome_params* p,
+                           void* stream);
+/* Same, with the ASCII genome already in device memory. */
+MSS_API mss_status mss_load_genome_device(mss_ctx** out, const char* d_seq, int64_t len, const mss_genome_params* p,
+                                  void* stream);
+MSS_API mss_status mss_get_info(const mss_ctx* ctx, mss_genome_info* info);
+/* Change F after loading (the packed genome does not depend on F). */
+MSS_API mss_status mss_set_frag_len(mss_ctx* ctx, int64_t frag_len);
+MSS_API mss_status mss_set_tune(mss_ctx* ctx, const mss_tune* t);
+MSS_API mss_status mss_get_tune(const mss_ctx* ctx, mss_tune* t);
+
+/*
+ * Phase one for R reads (host buffers): reads = concatenated ASCII, offsets[R+1] (int64,
+ * offsets[0] = 0, non-decreasing), each length 1..max_read_len.  out[R] receives the hits in
+ * input order.  Synchronous.
+ */
+MSS_API mss_status mss_map_reads(mss_ctx* ctx, const char* reads, const int64_t* offsets, int32_t R,
+                         const mss_score_params* sp, mss_hit* out, void* stream);
+/*
+ * Phase one, device buffers: d_reads, d_offsets[R+1], d_out[R] in device memory.  max_len
+ * is a host-side upper bound on the read lengths (<= the context's max_read_len).  The work
+ * is enqueued on the stream (as one CUDA graph when the stream is not the legacy default
+ * stream); the context may be reused only in stream order.  Device-side errors (bad
+ * character, bad length) are reported by mss_sync().
+ */
+MSS_API mss_status mss_map_reads_device(mss_ctx* ctx, const char* d_reads, const int64_t* d_offsets, int32_t R,
+                                int32_t max_len, const mss_score_params* sp, mss_hit* d_out, void* stream);
+
+/*
+ * Phase two for R reads (host buffers): hits from phase one, alignments out[R], CIGAR strings
+ * into cigar_buf (R slots of cigar_stride bytes, NUL-terminated, ops M/I/D).  Glocal (read
+ * end to end, genome ends free) affine-gap alignment of the read on hits[r].strand in the
+ * window [offset-W, offset+m+W) clipped to the genome, banded around the seed diagonal;
+ * traceback ties prefer a match/mismatch step, then a gap in the read (D), then a gap in the
+ * genome (I); a gap is closed in preference to extended; equal end scores -> smallest end.
+ */
+MSS_API mss_status nw_align(mss_ctx* ctx, const char* reads, const int64_t* offsets, int32_t R, const mss_hit* hits,
+                    const mss_nw_params* np, mss_aln* out, char* cigar_buf, int32_t cigar_stride, void* stream);
+/* Phase two, device buffers (enqueued, see mss_map_reads_device). */
+MSS_API mss_status nw_align_device(mss_ctx* ctx, const char* d_reads, const int64_t* d_offsets, int32_t R,
+                           int32_t max_len, const mss_hit* d_hits, const mss_nw_params* np, mss_aln* d_out,
+                           char* d_cigar_buf, int32_t cigar_stride, void* stream);
+
+/* Wait for the stream and return the first device-side error recorded since the last call. */
+MSS_API mss_status mss_sync(mss_ctx* ctx, void* stream);
+
+/*
+ * Pick the scan configuration (and, when allow_frag_len is non-zero, F among 1024, 2048,
+ * 4096, 8192) by timing phase one on the given device reads.  The result is stored in the
+ * context.  Changing F changes which fragments exist, so results depend on it.
+ */
+MSS_API mss_status mss_autotune(mss_ctx* ctx, const char* d_reads, const int64_t* d_offsets, int32_t R, int32_t max_len,
+                        const mss_score_params* sp, int32_t allow_frag_len, void* stream);
+
+/* Number of kernel launches enqueued by this context since it was created. */
+MSS_API int64_t mss_launch_count(const mss_ctx* ctx);
+
+/* Copy genome codes [start, start+n) (0..3 = ACGT, 4 = N/padding) into host memory, decoded
+   from the packed device genome (a check of the packing kernel). */
+MSS_API mss_status mss_genome_codes(const mss_ctx* ctx, int64_t start, int64_t n, uint8_t* out);
+
+/*
+ * Throughput probe of the two 16-bit SIMD pipes used by the scan: warp-instructions per SM
+ * clock of (0) packed-int16 DPX add-max, (1) f16x2 FMA with relu, (2) both interleaved.
+ * clk_mhz receives the SM clock the device reports.  Used for the roofline denominator.
+ */
+MSS_API mss_status mss_probe_pipes(double* rates3, double* clk_mhz);
+
+MSS_API void mss_free(mss_ctx* ctx);
+MSS_API const char* mss_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

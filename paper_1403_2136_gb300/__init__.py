@@ -1,0 +1,278 @@
+"""Python binding of libmaxss (MaxSSmap hot path on GB300).
+
+Argument marshalling only: every step of the mapping runs in the CUDA kernels of
+``libmaxss.so`` behind the C ABI declared in ``include/maxss.h``.  PyTorch is used for device
+memory and streams; numpy arrays are accepted for the host-pointer entry points.  There is no
+CPU fallback: importing this package fails loudly when the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmaxss.so")
+
+MSS_OK = 0
+MSS_EINVAL = -1
+MSS_ENOMEM = -2
+MSS_ECUDA = -3
+MSS_EREADLEN = -4
+MSS_EOVERFLOW = -5
+MSS_ETIMEOUT = -6
+MSS_ESTATE = -7
+MSS_MAX_READ_LEN = 2432
+MSS_NW_NONE = -2147483648
+MSS_HIT_REPEAT = 1
+
+# every symbol include/maxss.h declares
+EXPORTS = ("mss_load_genome", "mss_load_genome_device", "mss_get_info", "mss_set_frag_len", "mss_set_tune",
+           "mss_get_tune", "mss_map_reads", "mss_map_reads_device", "nw_align", "nw_align_device", "mss_sync",
+           "mss_autotune", "mss_launch_count", "mss_genome_codes", "mss_probe_pipes", "mss_free", "mss_last_error")
+
+HIT_DTYPE = np.dtype([("best_frag", np.int32), ("second_frag", np.int32), ("best_score", np.int32),
+                      ("second_score", np.int32), ("offset", np.int64), ("strand", np.int32), ("flags", np.int32)])
+ALN_DTYPE = np.dtype([("score", np.int32), ("cigar_len", np.int32), ("gstart", np.int64), ("gend", np.int64)])
+assert HIT_DTYPE.itemsize == 32 and ALN_DTYPE.itemsize == 24
+
+
+class MssError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where} failed with status {status}: {msg}")
+        self.status = status
+
+
+class GenomeParams(ctypes.Structure):
+    _fields_ = [("frag_len", ctypes.c_int64), ("max_read_len", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class ScoreParams(ctypes.Structure):
+    _fields_ = [("match", ctypes.c_int32), ("mismatch", ctypes.c_int32)]
+
+
+class NwParams(ctypes.Structure):
+    _fields_ = [("match", ctypes.c_int32), ("mismatch", ctypes.c_int32), ("gap_open", ctypes.c_int32),
+                ("gap_extend", ctypes.c_int32), ("band", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class GenomeInfo(ctypes.Structure):
+    _fields_ = [("genome_len", ctypes.c_int64), ("frag_len", ctypes.c_int64), ("num_frags", ctypes.c_int64),
+                ("padded_len", ctypes.c_int64), ("max_read_len", ctypes.c_int32), ("num_sms", ctypes.c_int32)]
+
+
+class Tune(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int32), ("pairs", ctypes.c_int32), ("queries", ctypes.c_int32),
+                ("ctas_per_sm", ctypes.c_int32), ("min_items_per_cta", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libmaxss.so (raises if it is missing: there is no fallback path)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libmaxss.so not built ({path}); run paper_1403_2136_gb300/build.py "
+                          "(or __graft_entry__.build()) on a machine with nvcc")
+    lib = ctypes.CDLL(path)
+    P, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    sig = {
+        "mss_load_genome": ([ctypes.POINTER(P), P, i64, ctypes.POINTER(GenomeParams), P], i32),
+        "mss_load_genome_device": ([ctypes.POINTER(P), P, i64, ctypes.POINTER(GenomeParams), P], i32),
+        "mss_get_info": ([P, ctypes.POINTER(GenomeInfo)], i32),
+        "mss_set_frag_len": ([P, i64], i32),
+        "mss_set_tune": ([P, ctypes.POINTER(Tune)], i32),
+        "mss_get_tune": ([P, ctypes.POINTER(Tune)], i32),
+        "mss_map_reads": ([P, P, P, i32, ctypes.POINTER(ScoreParams), P, P], i32),
+        "mss_map_reads_device": ([P, P, P, i32, i32, ctypes.POINTER(ScoreParams), P, P], i32),
+        "nw_align": ([P, P, P, i32, P, ctypes.POINTER(NwParams), P, P, i32, P], i32),
+        "nw_align_device": ([P, P, P, i32, i32, P, ctypes.POINTER(NwParams), P, P, i32, P], i32),
+        "mss_sync": ([P, P], i32),
+        "mss_autotune": ([P, P, P, i32, i32, ctypes.POINTER(ScoreParams), i32, P], i32),
+        "mss_launch_count": ([P], i64),
+        "mss_genome_codes": ([P, i64, i64, P], i32),
+        "mss_probe_pipes": ([ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], i32),
+        "mss_free": ([P], None),
+        "mss_last_error": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(st: int, where: str):
+    if st != MSS_OK:
+        raise MssError(st, where, (_lib.mss_last_error() or b"").decode(errors="replace"))
+
+
+def _host_ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return ctypes.c_void_p(a.ctypes.data)
+    # torch tensor (CPU pinned or device)
+    return ctypes.c_void_p(a.data_ptr())
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Genome:
+    """A packed genome on the device (owns the mss_ctx)."""
+
+    def __init__(self, handle):
+        self._h = handle
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        gi = GenomeInfo()
+        _check(_lib.mss_get_info(self._h, ctypes.byref(gi)), "mss_get_info")
+        return {f: getattr(gi, f) for f, _ in GenomeInfo._fields_}
+
+    def close(self):
+        if self._h:
+            _lib.mss_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mss_load_genome(seq, frag_len: int = 2048, max_read_len: int = MSS_MAX_READ_LEN, stream=None) -> Genome:
+    """Pack a genome.  seq: bytes / uint8 numpy array (host) or a uint8 CUDA tensor (device)."""
+    lib = load_library()
+    p = GenomeParams(frag_len, max_read_len, 0)
+    h = ctypes.c_void_p()
+    if isinstance(seq, (bytes, bytearray)):
+        seq = np.frombuffer(bytes(seq), dtype=np.uint8)
+    if isinstance(seq, np.ndarray):
+        seq = np.ascontiguousarray(seq, dtype=np.uint8)
+        st = lib.mss_load_genome(ctypes.byref(h), _host_ptr(seq), seq.shape[0], ctypes.byref(p), _stream_ptr(stream))
+        _check(st, "mss_load_genome")
+    else:
+        st = lib.mss_load_genome_device(ctypes.byref(h), _host_ptr(seq), int(seq.numel()), ctypes.byref(p),
+                                        _stream_ptr(stream))
+        _check(st, "mss_load_genome_device")
+    return Genome(h)
+
+
+def mss_set_frag_len(g: Genome, frag_len: int):
+    _check(load_library().mss_set_frag_len(g.handle, frag_len), "mss_set_frag_len")
+
+
+def mss_set_tune(g: Genome, variant=-1, pairs=0, queries=0, ctas_per_sm=0, min_items_per_cta=0):
+    t = Tune(variant, pairs, queries, ctas_per_sm, min_items_per_cta, 0)
+    _check(load_library().mss_set_tune(g.handle, ctypes.byref(t)), "mss_set_tune")
+
+
+def mss_get_tune(g: Genome) -> dict:
+    t = Tune()
+    _check(load_library().mss_get_tune(g.handle, ctypes.byref(t)), "mss_get_tune")
+    return {f: getattr(t, f) for f, _ in Tune._fields_}
+
+
+def mss_map_reads(g: Genome, reads, offsets, match: int, mismatch: int, out=None, stream=None) -> np.ndarray:
+    """Phase one, host buffers (numpy or pinned torch).  Returns the hits (HIT_DTYPE)."""
+    lib = load_library()
+    offsets = offsets if not isinstance(offsets, np.ndarray) else np.ascontiguousarray(offsets, dtype=np.int64)
+    R = (offsets.shape[0] if isinstance(offsets, np.ndarray) else offsets.numel()) - 1
+    if out is None:
+        out = np.zeros(R, dtype=HIT_DTYPE)
+    sp = ScoreParams(match, mismatch)
+    st = lib.mss_map_reads(g.handle, _host_ptr(reads), _host_ptr(offsets), R, ctypes.byref(sp), _host_ptr(out),
+                           _stream_ptr(stream))
+    _check(st, "mss_map_reads")
+    return out
+
+
+def mss_map_reads_device(g: Genome, d_reads, d_offsets, R: int, max_len: int, match: int, mismatch: int, d_out,
+                         stream=None):
+    """Phase one, device buffers: d_out is a CUDA tensor of at least 32*R bytes."""
+    sp = ScoreParams(match, mismatch)
+    st = load_library().mss_map_reads_device(g.handle, _host_ptr(d_reads), _host_ptr(d_offsets), R, max_len,
+                                             ctypes.byref(sp), _host_ptr(d_out), _stream_ptr(stream))
+    _check(st, "mss_map_reads_device")
+
+
+def nw_align(g: Genome, reads, offsets, hits: np.ndarray, match=5, mismatch=-4, gap_open=-26, gap_extend=-26,
+             band=32, cigar_stride=None, stream=None):
+    """Phase two, host buffers.  Returns (alns HIT array of ALN_DTYPE, list of CIGAR strings)."""
+    lib = load_library()
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    R = offsets.shape[0] - 1
+    if cigar_stride is None:
+        lens = np.diff(offsets)
+        cigar_stride = int(max(16, 4 * (int(lens.max()) if R else 1) + 64))
+    out = np.zeros(R, dtype=ALN_DTYPE)
+    cig = np.zeros((max(R, 1), cigar_stride), dtype=np.uint8)
+    npar = NwParams(match, mismatch, gap_open, gap_extend, band, 0)
+    st = lib.nw_align(g.handle, _host_ptr(reads), _host_ptr(offsets), R, _host_ptr(np.ascontiguousarray(hits)),
+                      ctypes.byref(npar), _host_ptr(out), _host_ptr(cig), cigar_stride, _stream_ptr(stream))
+    _check(st, "nw_align")
+    cigars = [bytes(cig[i, :max(out["cigar_len"][i], 0)]).decode() for i in range(R)]
+    return out, cigars
+
+
+def nw_align_device(g: Genome, d_reads, d_offsets, R: int, max_len: int, d_hits, d_out, d_cigars,
+                    cigar_stride: int, match=5, mismatch=-4, gap_open=-26, gap_extend=-26, band=32, stream=None):
+    npar = NwParams(match, mismatch, gap_open, gap_extend, band, 0)
+    st = load_library().nw_align_device(g.handle, _host_ptr(d_reads), _host_ptr(d_offsets), R, max_len,
+                                        _host_ptr(d_hits), ctypes.byref(npar), _host_ptr(d_out),
+                                        _host_ptr(d_cigars), cigar_stride, _stream_ptr(stream))
+    _check(st, "nw_align_device")
+
+
+def mss_sync(g: Genome, stream=None):
+    _check(load_library().mss_sync(g.handle, _stream_ptr(stream)), "mss_sync")
+
+
+def mss_autotune(g: Genome, d_reads, d_offsets, R: int, max_len: int, match: int, mismatch: int,
+                 allow_frag_len: bool = False, stream=None) -> dict:
+    sp = ScoreParams(match, mismatch)
+    st = load_library().mss_autotune(g.handle, _host_ptr(d_reads), _host_ptr(d_offsets), R, max_len,
+                                     ctypes.byref(sp), 1 if allow_frag_len else 0, _stream_ptr(stream))
+    _check(st, "mss_autotune")
+    return {**mss_get_tune(g), "frag_len": g.info()["frag_len"]}
+
+
+def mss_launch_count(g: Genome) -> int:
+    return int(load_library().mss_launch_count(g.handle))
+
+
+def mss_genome_codes(g: Genome, start: int, n: int) -> np.ndarray:
+    out = np.zeros(n, dtype=np.uint8)
+    _check(load_library().mss_genome_codes(g.handle, start, n, _host_ptr(out)), "mss_genome_codes")
+    return out
+
+
+def mss_probe_pipes():
+    """(dpx, fma, both) warp-instructions per SM clock, and the reported SM clock in MHz."""
+    r = (ctypes.c_double * 3)()
+    clk = ctypes.c_double()
+    _check(load_library().mss_probe_pipes(r, ctypes.byref(clk)), "mss_probe_pipes")
+    return list(r), clk.value
+
+
+def hits_from_bytes(buf) -> np.ndarray:
+    """View raw hit bytes (numpy uint8 or a CPU tensor) as HIT_DTYPE records."""
+    a = buf.numpy() if hasattr(buf, "numpy") else np.asarray(buf)
+    return a.view(HIT_DTYPE)

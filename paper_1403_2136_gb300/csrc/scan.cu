@@ -1,0 +1,495 @@
+// a3-a5: maximum-scoring-subsequence scan of every read (both strands) along every diagonal,
+// per-fragment maxima and the per-read top-2 fragments; then the best-fragment rescan that
+// recovers the best diagonal and strand.
+//
+// Method ("First phase of MaxSSmap", "Maximum scoring subsequence"): for a read q and
+// diagonal d, the substitution scores s_k = score(q[k], g[d+k]) are reduced by the linear
+// maximum-scoring-subsequence scan H = max(H + s, 0), M = max(M, H); fragment f keeps the
+// maximum M over its diagonals [fF, (f+1)F) (windows run into the next fragment); the read
+// keeps the best and the second-best fragment.
+//
+// GB300 design (not the paper's thread-per-fragment layout):
+//   * one work item = a group of RQ query sequences (RQ/2 reads x 2 strands) against one
+//     chunk of the genome; persistent CTAs pull items from a device queue, longest reads
+//     first;
+//   * a CTA tile is NT*2D consecutive diagonals; thread t owns diagonals t*2D + [0, 2D) as D
+//     packed 16-bit lane pairs (d, d + D) per query;
+//   * the 2-bit genome of a tile is staged by a bulk (TMA) copy into a double buffer and
+//     expanded once into PRMT selector words laid out [lane row][thread column] so that a warp
+//     reads 32 consecutive words (the same idea as the paper's transposed genome, Figure 2,
+//     done in shared memory);
+//   * the query profile (one byte per genome base per read position) sits in shared memory
+//     and is read as warp-wide broadcasts;
+//   * score generation is one PRMT per lane pair; the recurrence H runs either as a packed
+//     int16 DPX add-max (variant 0, any scores) or as a packed f16 FMA with relu on the FMA
+//     pipe (variant 1, exact for small integer scores); the running maximum M is a packed
+//     3-input DPX max every second step;
+//   * per-fragment maxima go through warp redux + shared-memory atomics into a ring of
+//     fragment slots, and completed fragments are folded by warp shuffles into a top-2
+//     summary per read; chunks are merged exactly by the finalize kernel.
+#include "../../include/maxss.h"
+#include "common.cuh"
+#include "internal.h"
+
+namespace mss {
+
+template <int D, int NT>
+struct ScanGeo {
+  static constexpr int kSpan = 2 * D;                                     // diagonals per thread
+  static constexpr int kTile = NT * kSpan;                                // diagonals per tile
+  static constexpr int kSelCols = (kTile + MSS_MAX_READ_LEN + 2 * D + kSpan - 1) / kSpan;
+  static constexpr int kRawPos = ((kTile + MSS_MAX_READ_LEN + 4 * D + 16 + 127) / 128) * 128;
+  static constexpr uint32_t kRawG2Bytes = kRawPos / 4;
+  static constexpr uint32_t kRawGmBytes = kRawPos / 8;
+  static constexpr uint32_t kRawBytes = kRawG2Bytes + kRawGmBytes;
+};
+
+struct SmemLayout {
+  size_t prof, sel, raw, ring, top, mbar, misc, total;
+};
+
+template <int D, int RQ, int NT>
+__host__ __device__ inline SmemLayout scan_layout(int32_t max_len, int32_t ring_slots) {
+  using Geo = ScanGeo<D, NT>;
+  SmemLayout L;
+  size_t mpad_max = (size_t)((max_len + 7) & ~7);
+  L.prof = 0;
+  L.sel = L.prof + mpad_max * RQ * 4;
+  L.raw = L.sel + (size_t)Geo::kSpan * Geo::kSelCols * 4;
+  L.raw = (L.raw + 127) & ~(size_t)127;
+  L.ring = L.raw + 2 * (size_t)Geo::kRawBytes;
+  L.top = L.ring + (size_t)(RQ / 2) * ring_slots * 4;
+  L.top = (L.top + 15) & ~(size_t)15;
+  L.mbar = L.top + (size_t)(RQ / 2) * sizeof(Top2);
+  L.misc = L.mbar + 16;                     // item (4 B), read lengths at +16, offsets at +32
+  L.total = L.misc + 32 + (size_t)(RQ / 2) * 8;
+  return L;
+}
+
+// PRMT selector for the lane pair (genome code c1 at d + k, code c2 at d + D + k).
+template <bool F16>
+__device__ __forceinline__ uint32_t make_sel(uint32_t c1, uint32_t c2) {
+  if (F16) {
+    // f16 lane = [low byte 0x00 (byte 4 of {b,a}), high byte = profile byte c, or byte 5 for N]
+    uint32_t n1 = c1 < 4 ? c1 : 5u, n2 = c2 < 4 ? c2 : 5u;
+    return 4u | (n1 << 4) | (4u << 8) | (n2 << 12);
+  } else {
+    // int16 lane = [profile byte c (byte 4 = mismatch for N), its sign replicated]
+    uint32_t n1 = c1 < 4 ? c1 : 4u, n2 = c2 < 4 ? c2 : 4u;
+    return n1 | ((n1 | 8u) << 4) | (n2 << 8) | ((n2 | 8u) << 12);
+  }
+}
+
+// Profile word of one query base: byte b = score byte of (query base, genome base b).
+__device__ __forceinline__ uint32_t profile_word(uint32_t code, uint32_t ma, uint32_t mm) {
+  uint32_t w = mm * 0x01010101u;
+  if (code < 4) w = (w & ~(0xFFu << (8 * code))) | (ma << (8 * code));
+  return w;
+}
+
+template <bool F16>
+__device__ __forceinline__ uint32_t kadane_step(uint32_t h, uint32_t s) {
+  if (F16) return hfma2_relu(h, 0x3C003C00u, s);   // relu(h * 1 + s) on two f16 lanes
+  return __viaddmax_s16x2(h, s, 0u);                // max(h + s, 0) on two int16 lanes
+}
+
+template <bool F16>
+__device__ __forceinline__ int32_t lane_value(uint32_t bits16) {
+  if (F16) return f16_bits_to_int(bits16);
+  return (int32_t)(int16_t)(bits16 & 0xFFFFu);
+}
+
+template <bool F16, int D, int RQ, int NT>
+__global__ void __launch_bounds__(NT, 2) k_scan(ScanArgs a) {
+  using Geo = ScanGeo<D, NT>;
+  constexpr int RG = RQ / 2;
+  constexpr int SPAN = Geo::kSpan;
+  constexpr int TILE = Geo::kTile;
+  constexpr int W = Geo::kSelCols;
+  static_assert(RQ % 4 == 0, "profile rows are read as uint4");
+  static_assert(D % 2 == 0, "the running max is updated every second step");
+  static_assert(RG <= 4, "read lengths occupy 16 bytes of the misc area");
+
+  extern __shared__ __align__(128) uint8_t smem[];
+  const SmemLayout L = scan_layout<D, RQ, NT>(a.max_len, a.ring_slots);
+  uint32_t* prof = reinterpret_cast<uint32_t*>(smem + L.prof);
+  uint32_t* sel = reinterpret_cast<uint32_t*>(smem + L.sel);
+  uint8_t* raw = smem + L.raw;
+  int32_t* ring = reinterpret_cast<int32_t*>(smem + L.ring);
+  Top2* top = reinterpret_cast<Top2*>(smem + L.top);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L.mbar);
+  int32_t* s_item = reinterpret_cast<int32_t*>(smem + L.misc);
+  int32_t* s_len = reinterpret_cast<int32_t*>(smem + L.misc + 16);      // [RG]
+  int64_t* s_off = reinterpret_cast<int64_t*>(smem + L.misc + 32);      // [RG]
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int S = a.ring_slots;
+  const uint32_t mmw = a.mm_word;
+
+  if (tid == 0) {
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  uint32_t parity[2] = {0u, 0u};
+  bool timed_out = false;
+
+  for (;;) {
+    if (tid == 0) *s_item = atomicAdd(a.queue, 1);
+    __syncthreads();
+    const int item = *s_item;
+    if (item >= a.n_items) break;
+    const int g = item / a.n_chunks;
+    const int c = item - g * a.n_chunks;
+
+    if (tid < RG) {
+      const int p = g * RG + tid;
+      int32_t len = 0;
+      int64_t off = 0;
+      if (p < a.R) {
+        const int ridx = a.order[p];
+        off = a.offsets[ridx];
+        int64_t l = a.offsets[ridx + 1] - off;
+        len = l < 0 ? 0 : (l > a.max_len ? a.max_len : (int32_t)l);
+      }
+      s_len[tid] = len;
+      s_off[tid] = off;
+      top[tid] = top2_empty();
+    }
+    for (int e = tid; e < RG * S; e += NT) ring[e] = 0;
+    __syncthreads();
+
+    int32_t mmax = 0;
+#pragma unroll
+    for (int r = 0; r < RG; ++r) mmax = max(mmax, s_len[r]);
+    const int mpad = max(D, (mmax + D - 1) / D * D);
+
+    // query profile: prof[k * RQ + q], q = 2r (forward) or 2r + 1 (reverse complement)
+    for (int e = tid; e < mpad * RQ; e += NT) {
+      const int k = e / RQ, q = e - k * RQ, r = q >> 1;
+      const int len = s_len[r];
+      uint32_t code = 4;
+      if (k < len) {
+        const int64_t pos = s_off[r] + ((q & 1) ? (len - 1 - k) : k);
+        code = ascii_code((uint8_t)a.reads[pos]);
+        if (code == 5) {
+          atomicOr(a.err, ERR_BAD_CHAR);
+          code = 4;
+        }
+        if ((q & 1) && code < 4) code = 3 - code;
+      }
+      prof[e] = profile_word(code, a.prof_match, a.prof_mismatch);
+    }
+
+    const int64_t c0 = (int64_t)c * a.chunk_len;
+    const int64_t c1 = min(c0 + a.chunk_len, a.Gp);
+    const int ntiles = (int)((c1 - c0 + TILE - 1) / TILE);
+    const int32_t f_lo = (int32_t)(c0 / a.F);
+    const int32_t f_end = (int32_t)((c1 - 1) / a.F) + 1;
+    int32_t fold_next = f_lo;
+
+    auto issue = [&](int t, int buf) {
+      const int64_t ts = c0 + (int64_t)t * TILE;
+      uint8_t* dst = raw + buf * Geo::kRawBytes;
+      fence_proxy_async_smem();
+      mbar_arrive_expect_tx(&mbar[buf], Geo::kRawBytes);
+      tma_load_1d(dst, reinterpret_cast<const uint8_t*>(a.g2) + ts / 4, Geo::kRawG2Bytes, &mbar[buf]);
+      tma_load_1d(dst + Geo::kRawG2Bytes, reinterpret_cast<const uint8_t*>(a.gm) + ts / 8, Geo::kRawGmBytes,
+                  &mbar[buf]);
+    };
+    auto fold = [&](int r, int32_t lo, int32_t hi) {  // fragments [lo, hi) of read r, one warp
+      Top2 acc = top2_empty();
+      for (int32_t base = lo; base < hi; base += 32) {
+        const int32_t f = base + lane;
+        if (f < hi) {
+          const int slot = r * S + (int)(f % S);
+          const int32_t v = ring[slot];
+          ring[slot] = 0;
+          acc = top2_merge(acc, Top2{v, f, -1, 0x7fffffff});
+        }
+      }
+#pragma unroll
+      for (int m = 16; m > 0; m >>= 1) acc = top2_merge(acc, top2_shfl_xor(acc, m));
+      if (lane == 0) top[r] = top2_merge(top[r], acc);
+    };
+
+    __syncthreads();  // profile and ring ready
+    if (tid == 0) issue(0, 0);
+
+    for (int t = 0; t < ntiles; ++t) {
+      const int buf = t & 1;
+      if (tid == 0 && t + 1 < ntiles) issue(t + 1, buf ^ 1);
+      if (!mbar_wait(&mbar[buf], parity[buf], 1u << 20)) timed_out = true;
+      parity[buf] ^= 1u;
+
+      // expand the staged 2-bit genome into selector words: sel[row * W + col] is the
+      // selector of tile position p = col * SPAN + row (codes at p and p + D)
+      {
+        const uint32_t* rg2 = reinterpret_cast<const uint32_t*>(raw + buf * Geo::kRawBytes);
+        const uint32_t* rgm = reinterpret_cast<const uint32_t*>(raw + buf * Geo::kRawBytes + Geo::kRawG2Bytes);
+        const int ncols = (TILE + mpad + D + SPAN - 1) / SPAN;
+        for (int e = tid; e < SPAN * ncols; e += NT) {
+          const int row = e / ncols, col = e - row * ncols;
+          const int p = col * SPAN + row;
+          const uint32_t q1 = (rg2[p >> 4] >> ((p & 15) * 2)) & 3u;
+          const uint32_t v1 = (rgm[p >> 5] >> (p & 31)) & 1u;
+          const int p2 = p + D;
+          const uint32_t q2 = (rg2[p2 >> 4] >> ((p2 & 15) * 2)) & 3u;
+          const uint32_t v2 = (rgm[p2 >> 5] >> (p2 & 31)) & 1u;
+          sel[row * W + col] = make_sel<F16>(v1 ? q1 : 4u, v2 ? q2 : 4u);
+        }
+      }
+      __syncthreads();
+
+      const int64_t ts = c0 + (int64_t)t * TILE;
+      {
+        const int64_t tf = ts / a.F;
+        const int32_t done = (int32_t)(tf < (int64_t)f_end ? tf : (int64_t)f_end);  // fragments < done are complete
+        if (warp < RG && done > fold_next) fold(warp, fold_next, done);
+        fold_next = max(fold_next, done);
+      }
+
+      // ---- the scan of this tile
+      uint32_t win[D];
+#pragma unroll
+      for (int j = 0; j < D; ++j) win[j] = sel[j * W + tid];
+      uint32_t H[RQ][D], Ha[RQ][D], M[RQ][D];
+#pragma unroll
+      for (int q = 0; q < RQ; ++q)
+#pragma unroll
+        for (int j = 0; j < D; ++j) H[q][j] = 0u, Ha[q][j] = 0u, M[q][j] = 0u;
+
+      for (int k0 = 0; k0 < mpad; k0 += D) {
+        // positions entering the window during this block: p = tid*SPAN + k0 + u + D, u < D,
+        // all in one selector row band and one column
+        const int kk = k0 + D;
+        const uint32_t* sp = sel + (kk % SPAN) * W + tid + kk / SPAN;
+        const uint4* pp = reinterpret_cast<const uint4*>(prof + k0 * RQ);
+#pragma unroll
+        for (int u = 0; u < D; ++u) {
+          uint32_t pw[RQ];
+#pragma unroll
+          for (int v = 0; v < RQ / 4; ++v) {
+            const uint4 x = pp[u * (RQ / 4) + v];
+            pw[4 * v + 0] = x.x;
+            pw[4 * v + 1] = x.y;
+            pw[4 * v + 2] = x.z;
+            pw[4 * v + 3] = x.w;
+          }
+#pragma unroll
+          for (int q = 0; q < RQ; ++q) {
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+              const uint32_t s = prmt(pw[q], mmw, win[(j + u) % D]);
+              if ((u & 1) == 0) {
+                Ha[q][j] = kadane_step<F16>(H[q][j], s);
+              } else {
+                const uint32_t h = kadane_step<F16>(Ha[q][j], s);
+                M[q][j] = __vimax3_s16x2(M[q][j], Ha[q][j], h);
+                H[q][j] = h;
+              }
+            }
+          }
+          win[u] = sp[u * W];
+        }
+      }
+
+      // ---- per-fragment maxima of this thread's 2D diagonals
+      const int64_t ds = ts + (int64_t)tid * SPAN;
+      const int32_t fA = (int32_t)(ds / a.F);
+      const int64_t bnd = (int64_t)(fA + 1) * a.F;
+      const bool split = ds + SPAN > bnd;
+      const int32_t fA0 = __shfl_sync(0xffffffffu, fA, 0);
+      const bool uni = __all_sync(0xffffffffu, (fA == fA0) && !split);
+      uint32_t maskA[D];
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        const uint32_t lo = (ds + j < bnd) ? 0x0000FFFFu : 0u;
+        const uint32_t hi = (ds + D + j < bnd) ? 0xFFFF0000u : 0u;
+        maskA[j] = split ? (lo | hi) : 0xFFFFFFFFu;
+      }
+#pragma unroll
+      for (int r = 0; r < RG; ++r) {
+        uint32_t xa = 0u, xb = 0u;
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+          xa = __vimax3_s16x2(xa, M[2 * r][j] & maskA[j], M[2 * r + 1][j] & maskA[j]);
+          xb = __vimax3_s16x2(xb, M[2 * r][j] & ~maskA[j], M[2 * r + 1][j] & ~maskA[j]);
+        }
+        const int32_t vA = max(lane_value<F16>(xa), lane_value<F16>(xa >> 16));
+        const int32_t vB = max(lane_value<F16>(xb), lane_value<F16>(xb >> 16));
+        if (uni) {
+          const int32_t v = __reduce_max_sync(0xffffffffu, vA);
+          if (lane == 0 && v > 0) atomicMax(&ring[r * S + (int)(fA0 % S)], v);
+        } else {
+          if (vA > 0) atomicMax(&ring[r * S + (int)(fA % S)], vA);
+          if (vB > 0) atomicMax(&ring[r * S + (int)((fA + 1) % S)], vB);
+        }
+      }
+      __syncthreads();
+    }
+
+    if (warp < RG && f_end > fold_next) fold(warp, fold_next, f_end);
+    __syncthreads();
+    if (tid < RG) {
+      const int p = g * RG + tid;
+      const Top2 v = top[tid];
+      a.partial[(size_t)p * a.n_chunks + c] = make_int4(v.s1, v.f1, v.s2, v.f2);
+    }
+    // the next item rewrites the profile, ring and summaries only after the barrier at its top
+  }
+  if (timed_out) atomicOr(a.err, ERR_TIMEOUT);
+}
+
+// ---------------------------------------------------------------- host side of the scan
+#define MSS_SCAN_VARIANTS(X) \
+  X(false, 4, 8, 256)        \
+  X(true, 4, 8, 256)         \
+  X(false, 8, 4, 256)        \
+  X(true, 8, 4, 256)         \
+  X(false, 4, 4, 256)        \
+  X(true, 4, 4, 256)
+
+template <bool F16, int D, int RQ, int NT>
+static const void* scan_fn() {
+  return reinterpret_cast<const void*>(&k_scan<F16, D, RQ, NT>);
+}
+
+static const void* pick_scan(const ScanConfig& c) {
+#define X(f, d, rq, nt) \
+  if (c.variant == (f ? 1 : 0) && c.pairs == d && c.queries == rq && c.threads == nt) return scan_fn<f, d, rq, nt>();
+  MSS_SCAN_VARIANTS(X)
+#undef X
+  return nullptr;
+}
+
+int64_t scan_tile_diags(const ScanConfig& c) { return (int64_t)c.threads * 2 * c.pairs; }
+
+size_t scan_smem_bytes(const ScanConfig& c, int32_t max_len, int32_t ring_slots) {
+#define X(f, d, rq, nt) \
+  if (c.pairs == d && c.queries == rq && c.threads == nt) return scan_layout<d, rq, nt>(max_len, ring_slots).total;
+  MSS_SCAN_VARIANTS(X)
+#undef X
+  return 0;
+}
+
+int scan_ring_slots(const ScanConfig& c, int64_t F) {
+  int64_t tile = scan_tile_diags(c);
+  int64_t per_tile = (tile + F - 1) / F;
+  int64_t s = 2 * per_tile + 4;
+  return (int)((s + 3) & ~3);  // multiple of 4 keeps the summaries 16-byte aligned
+}
+
+cudaError_t scan_max_ctas_per_sm(const ScanConfig& c, size_t smem, int* out) {
+  const void* fn = pick_scan(c);
+  if (!fn) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, fn, c.threads, smem);
+}
+
+cudaError_t launch_scan(const ScanConfig& c, const ScanArgs& a, int grid, size_t smem, cudaStream_t s) {
+  const void* fn = pick_scan(c);
+  if (!fn) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  void* args[] = {const_cast<ScanArgs*>(&a)};
+  return cudaLaunchKernel(fn, dim3(grid), dim3(c.threads), args, smem, s);
+}
+
+// ---------------------------------------------------------------- finalize: merge + rescan
+// One warp per read: merge the chunk summaries, then rescan the best fragment on both strands
+// with plain int32 arithmetic to find the best diagonal (ties: + strand first, then smallest
+// d).  The rescan costs 2*F*m cells per read (1/NF of the scan).
+constexpr int kFinWarps = 4;
+constexpr int kFinChunk = 1024;  // diagonals staged per pass
+
+__global__ void __launch_bounds__(kFinWarps * 32) k_finalize(FinalArgs a) {
+  __shared__ uint8_t s_gen[kFinWarps][kFinChunk + MSS_MAX_READ_LEN + 16];
+  __shared__ uint8_t s_q[kFinWarps][2][MSS_MAX_READ_LEN];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int p = blockIdx.x * kFinWarps + wib;
+  if (p >= a.R) return;
+  const int ridx = a.order[p];
+  const int64_t off = a.offsets[ridx];
+  int64_t l = a.offsets[ridx + 1] - off;
+  const int32_t m = l < 0 ? 0 : (l > MSS_MAX_READ_LEN ? MSS_MAX_READ_LEN : (int32_t)l);
+
+  Top2 acc = top2_empty();
+  for (int c = lane; c < a.n_chunks; c += 32) {
+    const int4 v = a.partial[(size_t)p * a.n_chunks + c];
+    acc = top2_merge(acc, Top2{v.x, v.y, v.z, v.w});
+  }
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1) acc = top2_merge(acc, top2_shfl_xor(acc, s));
+
+  for (int k = lane; k < m; k += 32) {
+    uint32_t cf = ascii_code((uint8_t)a.reads[off + k]);
+    if (cf > 4) cf = 4;
+    s_q[wib][0][k] = (uint8_t)cf;
+    s_q[wib][1][m - 1 - k] = (uint8_t)(cf < 4 ? 3 - cf : 4);
+  }
+  __syncwarp();
+
+  const int32_t f1 = acc.f1;
+  int32_t bestK = -1, bestS = 0;
+  int64_t bestD = 0;
+  const int64_t d_lo = (int64_t)f1 * a.F, d_hi = d_lo + a.F;
+  for (int sg = 0; sg < 2; ++sg) {
+    for (int64_t d0 = d_lo; d0 < d_hi; d0 += kFinChunk) {
+      const int64_t nd = (d_hi - d0 < (int64_t)kFinChunk) ? d_hi - d0 : (int64_t)kFinChunk;
+      __syncwarp();
+      for (int64_t i = lane; i < nd + m; i += 32) s_gen[wib][i] = (uint8_t)genome_code(a.g2, a.gm, d0 + i);
+      __syncwarp();
+      for (int64_t i = lane; i < nd; i += 32) {
+        int32_t h = 0, mx = 0;
+        for (int k = 0; k < m; ++k) {
+          const uint32_t qc = s_q[wib][sg][k], gc = s_gen[wib][i + k];
+          h += (qc < 4 && qc == gc) ? a.match : a.mismatch;
+          h = max(h, 0);
+          mx = max(mx, h);
+        }
+        if (mx > bestK) {  // lanes visit (strand, d) in increasing order
+          bestK = mx;
+          bestS = sg;
+          bestD = d0 + i;
+        }
+      }
+    }
+  }
+  // warp argmax: larger K, then smaller strand, then smaller d
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1) {
+    const int32_t oK = __shfl_xor_sync(0xffffffffu, bestK, s);
+    const int32_t oS = __shfl_xor_sync(0xffffffffu, bestS, s);
+    const int64_t oD = __shfl_xor_sync(0xffffffffu, bestD, s);
+    if (oK > bestK || (oK == bestK && (oS < bestS || (oS == bestS && oD < bestD)))) {
+      bestK = oK;
+      bestS = oS;
+      bestD = oD;
+    }
+  }
+  if (lane == 0) {
+    if (bestK != acc.s1) atomicOr(a.err, ERR_SELFCHECK);
+    mss_hit h;
+    h.best_frag = acc.f1;
+    h.best_score = acc.s1;
+    h.second_frag = acc.s2 < 0 ? -1 : acc.f2;
+    h.second_score = acc.s2 < 0 ? 0 : acc.s2;
+    h.offset = bestD;
+    h.strand = bestS;
+    const bool repeat = (h.best_score == 0) || (10LL * h.second_score >= 9LL * h.best_score);
+    h.flags = repeat ? MSS_HIT_REPEAT : 0;
+    reinterpret_cast<mss_hit*>(a.hits)[ridx] = h;
+  }
+}
+
+cudaError_t launch_finalize(const FinalArgs& a, cudaStream_t s) {
+  if (a.R <= 0) return cudaSuccess;
+  const int blocks = (a.R + kFinWarps - 1) / kFinWarps;
+  k_finalize<<<blocks, kFinWarps * 32, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace mss

@@ -1,0 +1,209 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle, element by element.
+
+Integer and index results must be bit-exact (best/second fragment, scores, offset, strand,
+flags; NW score, span and CIGAR).
+"""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+from tests.parity_util import (assert_alns_equal, assert_hits_equal, concat_reads, cpu_count, oracle_map)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mss():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_1403_2136_gb300 as m
+    from paper_1403_2136_gb300 import build
+    build.build()
+    m.load_library()
+    return m
+
+
+def run_both(mss, genome, seq, off, F, match, mismatch, nw=None, max_len=None, tune=None, procs=None):
+    g = mss.mss_load_genome(genome, frag_len=F, max_read_len=max_len or max(1, int(np.diff(off).max())))
+    if tune:
+        mss.mss_set_tune(g, **tune)
+    hits = mss.mss_map_reads(g, seq, off, match, mismatch)
+    alns = cig = None
+    if nw is not None:
+        alns, cig = mss.nw_align(g, seq, off, hits, *nw)
+    ohits, oalns, ocig = oracle_map(genome, F, seq, off, match, mismatch, nw=nw, procs=procs)
+    g.close()
+    return hits, alns, cig, ohits, oalns, ocig
+
+
+def test_pack_matches_oracle_encoding(mss):
+    rng = np.random.default_rng(1)
+    G = 100_003
+    genome = rng.choice(np.frombuffer(b"ACGTNacgtn", np.uint8), size=G)
+    g = mss.mss_load_genome(genome, frag_len=1000, max_read_len=100)
+    codes = mss.mss_genome_codes(g, 0, G + 500)
+    assert np.array_equal(codes[:G], oracle.encode(genome))
+    assert np.all(codes[G:] == 4)      # padding reads as N
+    g.close()
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_tiny_50k_all_reads(mss, variant):
+    """50 kbp uniform genome, F=1000, 100 x 100 bp reads (10% subs + one indel), +1/-1."""
+    wl = gen.workloads()["tiny-50k"]
+    genome, reads = gen.materialize(wl)
+    hits, alns, cig, oh, oa, oc = run_both(mss, genome, reads.seq, reads.offsets, wl.frag_len, wl.match,
+                                           wl.mismatch, nw=wl.nw, tune={"variant": variant}, procs=cpu_count())
+    assert_hits_equal(hits, oh, f"tiny-50k variant {variant}")
+    assert_alns_equal(alns, cig, oa, oc, f"tiny-50k variant {variant}")
+    # the generator's truth: most reads map to the fragment of their true start
+    assert np.mean(hits["best_frag"] == reads.true_start // wl.frag_len) > 0.8
+
+
+@pytest.mark.parametrize("pairs,queries", [(4, 8), (8, 4), (4, 4)])
+@pytest.mark.parametrize("variant", [0, 1])
+def test_scan_configurations(mss, pairs, queries, variant):
+    wl = gen.scaled(gen.workloads()["bact-4.6M"], genome_len=60_000, reads=37)
+    genome, reads = gen.materialize(wl)
+    hits, _, _, oh, _, _ = run_both(mss, genome, reads.seq, reads.offsets, 1000, 5, -4,
+                                    tune={"variant": variant, "pairs": pairs, "queries": queries},
+                                    procs=cpu_count())
+    assert_hits_equal(hits, oh, f"config v{variant} D{pairs} Q{queries}")
+
+
+@pytest.mark.parametrize("items", [1, 4, 64])
+def test_chunking_is_result_neutral(mss, items):
+    """One chunk per group, a few, or many chunks per group must give the same top-2 (the
+    cross-chunk merge of fragments split between chunks is exact)."""
+    wl = gen.scaled(gen.workloads()["bact-4.6M"], genome_len=90_000, reads=20)
+    genome, reads = gen.materialize(wl)
+    hits, _, _, oh, _, _ = run_both(mss, genome, reads.seq, reads.offsets, 777, 5, -4,
+                                    tune={"min_items_per_cta": items}, procs=cpu_count())
+    assert_hits_equal(hits, oh, f"items {items}")
+
+
+def test_adversarial_cases(mss):
+    rng = np.random.default_rng(7)
+    G = 20_000
+    genome = bytearray(rng.choice(np.frombuffer(b"ACGT", np.uint8), size=G).tobytes())
+    genome[3000:3400] = genome[12000:12400]           # exact repeat (ties -> lowest fragment)
+    genome[7000:7700] = b"N" * 700                    # an all-N stretch covering whole fragments
+    genome[15000:15300] = genome[15000:15300].lower()  # lowercase bases are bases
+    genome = bytes(genome)
+    reads = [
+        genome[12050:12150],                           # repeat copy: best == second, repeat flag
+        genome[0:60],                                  # genome start
+        genome[G - 45:G],                              # genome end (window runs into padding)
+        genome[G - 20:G] + b"ACGTACGTAC",              # overhangs the genome end
+        genome[7100:7200],                             # all N
+        b"N" * 33,                                     # read of N only: best == 0
+        genome[4990:5020],                             # junction of fragments (F = 250 below)
+        genome[15010:15110],                           # lowercase source
+        b"A",                                          # m = 1
+        b"GT",                                         # m = 2
+        genome[100:131], genome[200:232], genome[300:333],  # m = 31, 32, 33
+        genome[400:650],                               # m = 250
+        bytes(rng.choice(np.frombuffer(b"ACGTN", np.uint8), size=97).tobytes()),
+    ]
+    seq, off = concat_reads(reads)
+    for F in (250, 16, 1000, 20_000, 30_000):         # F = G and F > G: a single fragment
+        for (ma, mm) in ((5, -4), (1, -1), (13, -7), (3, 0)):
+            hits, _, _, oh, _, _ = run_both(mss, genome, seq, off, F, ma, mm, max_len=300, procs=1)
+            assert_hits_equal(hits, oh, f"adversarial F={F} scores {ma}/{mm}")
+            if F == 250:   # the exact repeat copy ties with its source
+                assert oh["best_score"][0] == oh["second_score"][0] and oh["flags"][0] == 1
+                assert oh["best_score"][5] == 0 and oh["flags"][5] == 1
+            if F > 20_000:  # a single fragment: no second
+                assert np.all(oh["second_frag"] == -1) and np.all(oh["second_score"] == 0)
+
+
+def test_longest_reads(mss):
+    """m up to the ABI maximum 2432 (int16 path: 2432 * 13 <= 32767)."""
+    rng = np.random.default_rng(8)
+    genome = rng.choice(np.frombuffer(b"ACGT", np.uint8), size=9000).tobytes()
+    reads = [genome[100:100 + 2432], genome[5000:5000 + 2000], genome[3000:3000 + 1024]]
+    reads = [bytes(r[:i] + (b"T" if r[i:i + 1] != b"T" else b"A") + r[i + 1:]) for r, i in zip(reads, (7, 99, 512))]
+    seq, off = concat_reads(reads)
+    for ma, mm in ((13, -2), (1, -1)):
+        hits, _, _, oh, _, _ = run_both(mss, genome, seq, off, 512, ma, mm, max_len=2432, procs=3)
+        assert_hits_equal(hits, oh, f"long reads {ma}/{mm}")
+
+
+def test_nw_parameters(mss):
+    wl = gen.scaled(gen.workloads()["bact-4.6M"], genome_len=40_000, reads=30)
+    genome, reads = gen.materialize(wl)
+    for nw in ((5, -4, -26, -26, 32), (5, -4, -10, -1, 32), (2, -3, -5, -2, 8), (5, -4, -10, -1, 63),
+               (1, -1, -1, -1, 0)):
+        hits, alns, cig, oh, oa, oc = run_both(mss, genome, reads.seq, reads.offsets, 2048, 5, -4, nw=nw,
+                                               procs=cpu_count())
+        assert_hits_equal(hits, oh, f"nw {nw}")
+        assert_alns_equal(alns, cig, oa, oc, f"nw {nw}")
+
+
+def test_device_path_and_graph_replay(mss):
+    import torch
+    wl = gen.scaled(gen.workloads()["bact-4.6M"], genome_len=50_000, reads=64)
+    genome, reads = gen.materialize(wl)
+    g = mss.mss_load_genome(genome, frag_len=2048, max_read_len=150)
+    d_seq = torch.from_numpy(reads.seq).cuda()
+    d_off = torch.from_numpy(reads.offsets).cuda()
+    R = reads.count
+    d_hits = torch.zeros(R * 32, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        for _ in range(3):   # capture once, replay
+            d_hits.zero_()
+            mss.mss_map_reads_device(g, d_seq, d_off, R, 150, 5, -4, d_hits, stream=s)
+            mss.mss_sync(g, stream=s)
+            got = mss.hits_from_bytes(d_hits.cpu())
+            want = mss.mss_map_reads(g, reads.seq, reads.offsets, 5, -4)
+            assert_hits_equal(got, want, "device path")
+    n1 = mss.mss_launch_count(g)
+    assert n1 >= 15
+    g.close()
+
+
+def test_errors_are_reported(mss):
+    genome = b"ACGT" * 100
+    g = mss.mss_load_genome(genome, frag_len=64, max_read_len=100)
+    seq, off = concat_reads([b"ACGTX"])
+    with pytest.raises(mss.MssError) as e:
+        mss.mss_map_reads(g, seq, off, 5, -4)
+    assert e.value.status == mss.MSS_EINVAL
+    seq, off = concat_reads([b"A" * 101])
+    with pytest.raises(mss.MssError) as e:
+        mss.mss_map_reads(g, seq, off, 5, -4)
+    assert e.value.status == mss.MSS_EREADLEN
+    seq, off = concat_reads([b"ACGT"])
+    with pytest.raises(mss.MssError) as e:
+        mss.mss_map_reads(g, seq, off, 0, -4)
+    assert e.value.status == mss.MSS_EINVAL
+    g.close()
+    g = mss.mss_load_genome(genome, frag_len=64, max_read_len=2432)
+    seq, off = concat_reads([b"A" * 2432])
+    with pytest.raises(mss.MssError) as e:
+        mss.mss_map_reads(g, seq, off, 14, -4)
+    assert e.value.status == mss.MSS_EOVERFLOW
+    with pytest.raises(mss.MssError):
+        mss.mss_load_genome(b"ACGTQ", frag_len=64)
+    # the context stays usable after an error
+    seq, off = concat_reads([b"ACGTACGT"])
+    h = mss.mss_map_reads(g, seq, off, 5, -4)
+    assert h["best_score"][0] == 40
+    g.close()
+
+
+def test_autotune_keeps_results(mss):
+    import torch
+    wl = gen.scaled(gen.workloads()["bact-4.6M"], genome_len=80_000, reads=48)
+    genome, reads = gen.materialize(wl)
+    g = mss.mss_load_genome(genome, frag_len=2048, max_read_len=150)
+    before = mss.mss_map_reads(g, reads.seq, reads.offsets, 5, -4)
+    d_seq = torch.from_numpy(reads.seq).cuda()
+    d_off = torch.from_numpy(reads.offsets).cuda()
+    t = mss.mss_autotune(g, d_seq, d_off, reads.count, 150, 5, -4, allow_frag_len=False)
+    assert t["frag_len"] == 2048
+    after = mss.mss_map_reads(g, reads.seq, reads.offsets, 5, -4)
+    assert_hits_equal(after, before, "autotune")
+    g.close()
