@@ -24,8 +24,12 @@ constexpr int32_t kNeg = -(1 << 29);        // "minus infinity" (finite scores s
 
 __device__ __forceinline__ int32_t clampneg(int32_t x) { return x < kNeg / 2 ? kNeg : x; }
 
+// Per-warp scratch: (max_len + 1) direction rows of 128 bytes, then the traceback ops
+// (at most m + window length <= 2m + 2W).  Rounded to 128 bytes so that every warp's rows stay
+// aligned for the 4-byte stores.
 int64_t nw_scratch_per_warp(int32_t max_len, int32_t band) {
-  return (int64_t)(max_len + 1) * kNwRow + 2 * (int64_t)max_len + 2 * (int64_t)band + 64;
+  const int64_t bytes = (int64_t)(max_len + 1) * kNwRow + 2 * (int64_t)max_len + 2 * (int64_t)band + 64;
+  return (bytes + 127) / 128 * 128;
 }
 
 __global__ void __launch_bounds__(kNwWarps * 32) k_nw(NwArgs a) {
