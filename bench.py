@@ -1,0 +1,357 @@
+#!/usr/bin/env python
+"""Benchmark of the MaxSSmap hot path on GB300 (one JSON line on rank 0).
+
+One step = the whole hot path over one batch: phase one (exact MSS scan of every read on
+both strands along every genome diagonal, per-fragment maxima, top-2 fragments, best-diagonal
+rescan) and phase two (banded NW) for every read of the workload.  Default workload: the
+bacterial-genome shape, a 4.6 Mbp synthetic genome (GC 50.8%, 2% exact 1-5 kbp repeat
+copies), F = 2048, 200,000 reads of 100 bp and 200,000 of 150 bp at 10/20/30% substitutions
+with up to two geometric gaps <= 30 bp, scores 5/-4, banded NW 5/-4/-10/-1 with W = 32.
+
+Metric: GCUPS = sum over reads of m * Gp * 2 strands / step time (the paper reports
+wall-clock minutes; cells per second is the standard unit of alignment scans), and reads/s.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mine|reference]
+
+--impl reference times the CPU oracle (the plain definition, single-threaded C, run as one
+process per host core over read shards) on a bounded sample of the same workload.
+Multi-GPU (torchrun): every rank maps its own batch of reads against its own genome replica
+(independent problems, weak scaling, no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+from concurrent.futures import ProcessPoolExecutor
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import gen  # noqa: E402
+
+METRIC = "GCUPS (exact MSS scan of every read, both strands, every diagonal + top-2 + banded NW)"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--workload", default="bact-4.6M")
+    ap.add_argument("--reads", type=int, default=0, help="override the read count (testing only)")
+    ap.add_argument("--genome", type=int, default=0, help="override the genome length (testing only)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-reads-per-core", type=int, default=2)
+    return ap.parse_args()
+
+
+def workload(args, rank: int):
+    wl = gen.workloads()[args.workload]
+    if args.reads or args.genome:
+        wl = gen.scaled(wl, genome_len=args.genome or None, reads=args.reads or None)
+    wl.seed = wl.seed  # genome identical on every rank; reads drawn per rank below
+    genome = gen.make_genome(wl.genome, wl.seed)
+    parts = [gen.make_reads(genome, rs, wl.seed * 31 + i + 1000003 * rank) for i, rs in enumerate(wl.reads)]
+    seq = np.concatenate([p.seq for p in parts])
+    lens = np.concatenate([p.lengths for p in parts]).astype(np.int64)
+    off = np.zeros(lens.shape[0] + 1, dtype=np.int64)
+    np.cumsum(lens, out=off[1:])
+    return wl, genome, seq, off
+
+
+def cells_of(lengths: np.ndarray, G: int, F: int) -> int:
+    Gp = -(-G // F) * F
+    return int(lengths.astype(np.int64).sum()) * Gp * 2
+
+
+# ------------------------------------------------------------------------------- CPU oracle
+def _oracle_job(args):
+    import oracle
+    genome, F, seq, off, match, mismatch, nw = args
+    oracle.map_batch(genome, F, seq, off, match, mismatch, nw=nw)
+    return int(off.shape[0] - 1)
+
+
+def cpu_sample(seq, off, n):
+    R = off.shape[0] - 1
+    idx = np.linspace(0, R - 1, n).astype(np.int64)
+    lens = (off[idx + 1] - off[idx]).astype(np.int64)
+    o = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(lens, out=o[1:])
+    s = np.concatenate([seq[off[i]:off[i + 1]] for i in idx])
+    return s, o
+
+
+def time_oracle(wl, genome, seq, off, cores, reads_per_core, pool):
+    n = max(1, cores * reads_per_core)
+    s, o = cpu_sample(seq, off, n)
+    bounds = np.linspace(0, n, cores + 1).astype(int)
+    jobs = []
+    for a, b in zip(bounds[:-1], bounds[1:]):
+        if b <= a:
+            continue
+        jobs.append((genome, wl.frag_len, np.ascontiguousarray(s[o[a]:o[b]]),
+                     np.ascontiguousarray(o[a:b + 1] - o[a]), wl.match, wl.mismatch, wl.nw))
+    t0 = time.perf_counter()
+    done = sum(pool.map(_oracle_job, jobs))
+    dt = time.perf_counter() - t0
+    cells = cells_of(np.diff(o), genome.shape[0], wl.frag_len)
+    return cells, done, dt
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    wl, genome, seq, off = workload(args, 0)
+    cores = host_cores()
+    with ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn")) as pool:
+        for _ in range(args.warmup):
+            time_oracle(wl, genome, seq, off, cores, 1, pool)
+        tot_cells = tot_reads = 0
+        tot_t = 0.0
+        for _ in range(args.steps):
+            c, r, dt = time_oracle(wl, genome, seq, off, cores, 1, pool)
+            tot_cells += c
+            tot_reads += r
+            tot_t += dt
+    gcups = tot_cells / tot_t / 1e9
+    sample = (f"{cores} reads per step (one per core, evenly spaced over the workload's 100/150 bp reads), "
+              f"phase one + banded NW")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(gcups, 4), "unit": "GCUPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(tot_t / args.steps * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": wl.name, "genome_bp": int(genome.shape[0]), "frag_len": wl.frag_len},
+        "reads_per_s": round(tot_reads / tot_t, 3),
+        "cpu_baseline": {"value": round(gcups, 4), "unit": "GCUPS", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(gcups, 4), "unit": "GCUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={','.join(self.FIELDS)}",
+                                          "--format=csv,noheader,nounits", "-lms", "200", "-i", str(gpu_index)],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                sm.append(float(p[0]))
+                mx.append(float(p[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------- GPU arm
+def peak_tcups(sms: int, clk_mhz: float) -> float:
+    """Roofline of the scan: 2 int16 ops per cell (add-relu, max); packed 16-bit x2 work runs on
+    two pipes of 16 lanes per SM sub-partition each (integer/DPX pipe and FMA pipe), so at most
+    2 pipes x 16 lanes x 2 halves / 2 ops = 32 cells per clock per sub-partition, 4 per SM."""
+    return sms * 4 * 32 * clk_mhz * 1e6 / 1e12
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+
+    import paper_1403_2136_gb300 as mss
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    wl, genome, seq, off = workload(args, rank)
+    lengths = np.diff(off)
+    R = int(lengths.shape[0])
+    max_len = int(lengths.max())
+    nm, nmm, go, ge, W = wl.nw
+    cells_step = cells_of(lengths, genome.shape[0], wl.frag_len)
+
+    # CPU baseline first (rank 0, N = 1), before the GPU is busy
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cores = host_cores()
+        with ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn")) as pool:
+            c, r, dt = time_oracle(wl, genome, seq, off, cores, args.cpu_reads_per_core, pool)
+        cpu = {"value": round(c / dt / 1e9, 4), "unit": "GCUPS", "cores": cores, "kind": "oracle",
+               "sample": f"{r} reads ({args.cpu_reads_per_core} per core, evenly spaced over the workload), "
+                         f"phase one + banded NW, {dt:.1f} s wall on {cores} processes",
+               "reads_per_s": round(r / dt, 3)}
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    props = torch.cuda.get_device_properties(dev)
+    g = mss.mss_load_genome(genome, frag_len=wl.frag_len, max_read_len=max_len)
+    info = g.info()
+    mss.mss_scan_timing(g, True)
+    stream = torch.cuda.Stream(device=dev)
+    d_seq = torch.from_numpy(seq).to(dev)
+    d_off = torch.from_numpy(off).to(dev)
+    d_hits = torch.empty(R * 32, dtype=torch.uint8, device=dev)
+    d_alns = torch.empty(R * 24, dtype=torch.uint8, device=dev)
+    stride = 4 * max_len + 64
+    d_cig = torch.empty(R * stride, dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def step():
+        mss.mss_map_reads_device(g, d_seq, d_off, R, max_len, wl.match, wl.mismatch, d_hits, stream=stream)
+        mss.nw_align_device(g, d_seq, d_off, R, max_len, d_hits, d_alns, d_cig, stride, nm, nmm, go, ge, W,
+                            stream=stream)
+
+    with torch.cuda.stream(stream):
+        for i in range(args.warmup):
+            step()
+        mss.mss_sync(g, stream=stream)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        scan_ms = []
+        clocks = ClockSampler(local) if rank == 0 else None
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        launches0 = mss.mss_launch_count(g)
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)                    # evict the genome and workspaces from L2
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+            scan_ms.append(mss.mss_scan_time_ms(g))  # waits for this step's scan
+        torch.cuda.synchronize(dev)
+        launches = mss.mss_launch_count(g) - launches0
+        if world > 1:
+            dist.barrier()
+        clk = clocks.stop() if clocks else None
+        mss.mss_sync(g, stream=stream)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_local = sum(step_ms) / 1e3
+    t = t_local
+    if world > 1:
+        tt = torch.tensor([t_local], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    total_cells = cells_step * args.steps * world
+    gcups = total_cells / t / 1e9
+    reads_s = R * args.steps * world / t
+
+    # end to end through the host-pointer call (pinned host buffers, copies inside the timing)
+    e2e = None
+    if not args.no_e2e:
+        h_seq = torch.from_numpy(seq).pin_memory()
+        h_off = torch.from_numpy(off).pin_memory()
+        h_hits = torch.empty(R * 32, dtype=torch.uint8).pin_memory()
+        h_alns = torch.empty(R * 24, dtype=torch.uint8).pin_memory()
+        h_cig = torch.empty(R * stride, dtype=torch.uint8).pin_memory()
+        mss.mss_map_align(g, h_seq, h_off, wl.match, wl.mismatch, wl.nw, h_hits, h_alns, h_cig, stride,
+                          stream=stream)
+        if world > 1:
+            dist.barrier()
+        e2e_steps = max(1, args.steps)
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            mss.mss_map_align(g, h_seq, h_off, wl.match, wl.mismatch, wl.nw, h_hits, h_alns, h_cig, stride,
+                              stream=stream)
+        te = time.perf_counter() - t0
+        if world > 1:
+            tt = torch.tensor([te], dtype=torch.float64, device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            te = float(tt.item())
+        e2e = {"value": round(cells_step * e2e_steps * world / te / 1e9, 3), "unit": "GCUPS",
+               "h2d_bytes_per_step": int(seq.nbytes + off.nbytes),
+               "d2h_bytes_per_step": int(R * 32 + R * 24 + R * stride),
+               "reads_per_s": round(R * e2e_steps * world / te, 1)}
+
+    if rank == 0:
+        sms = props.multi_processor_count
+        peak = peak_tcups(sms, 2070.0)
+        scan_mean_ms = statistics.mean(scan_ms)
+        achieved = cells_step / (scan_mean_ms * 1e-3) / 1e12
+        tune = mss.mss_get_tune(g)
+        line = {
+            "metric": METRIC, "value": round(gcups, 3), "unit": "GCUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(t * 1e3 / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int16", "data": "synthetic",
+            "config": {"workload": wl.name, "genome_bp": int(genome.shape[0]), "frag_len": wl.frag_len,
+                       "padded_bp": info["padded_len"], "reads": R, "read_lengths": sorted(set(lengths.tolist())),
+                       "scores": [wl.match, wl.mismatch], "nw": list(wl.nw),
+                       "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
+                       "parallelism": f"replicas x{world} (read batches per GPU)", "scan_tune": tune},
+            "reads_per_s": round(reads_s, 1),
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "roofline": {"bound": "alu", "kernel": "k_scan (phase-one scan + fragment top-2)",
+                         "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "Tcell/s",
+                         "frac": round(achieved / peak, 4), "traffic": None,
+                         "peak_source": f"derived: {sms} SMs x 4 sub-partitions x 32 cells/clk (16-lane integer/DPX "
+                                        "pipe + 16-lane FMA pipe, packed 16-bit x2, 2 ops per cell) x 2070 MHz",
+                         "scan_ms_per_step": round(scan_mean_ms, 3)},
+            "cpu_baseline": cpu,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    g.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -169,6 +169,15 @@ MSS_API mss_status nw_align_device(mss_ctx* ctx, const char* d_reads, const int6
                            int32_t max_len, const mss_hit* d_hits, const mss_nw_params* np, mss_aln* d_out,
                            char* d_cigar_buf, int32_t cigar_stride, void* stream);
 
+/*
+ * Both phases for R reads with host buffers and one upload: reads/offsets as in
+ * mss_map_reads; hits[R], alns[R] and cigar_buf (R slots of cigar_stride bytes) receive the
+ * results.  Synchronous.  This is the end-to-end call (host -> device -> host).
+ */
+MSS_API mss_status mss_map_align(mss_ctx* ctx, const char* reads, const int64_t* offsets, int32_t R,
+                                 const mss_score_params* sp, const mss_nw_params* np, mss_hit* hits, mss_aln* alns,
+                                 char* cigar_buf, int32_t cigar_stride, void* stream);
+
 /* Wait for the stream and return the first device-side error recorded since the last call. */
 MSS_API mss_status mss_sync(mss_ctx* ctx, void* stream);
 
@@ -179,6 +188,14 @@ MSS_API mss_status mss_sync(mss_ctx* ctx, void* stream);
  */
 MSS_API mss_status mss_autotune(mss_ctx* ctx, const char* d_reads, const int64_t* d_offsets, int32_t R, int32_t max_len,
                         const mss_score_params* sp, int32_t allow_frag_len, void* stream);
+
+/*
+ * Kernel timing of the scan: when enabled, every phase-one call records two CUDA events on its
+ * stream immediately around the scan kernel (inside the captured graph as event nodes).
+ * mss_scan_time_ms() waits for the last recorded pair and returns the scan kernel's duration.
+ */
+MSS_API mss_status mss_scan_timing(mss_ctx* ctx, int32_t enable);
+MSS_API mss_status mss_scan_time_ms(mss_ctx* ctx, float* ms);
 
 /* Number of kernel launches enqueued by this context since it was created. */
 MSS_API int64_t mss_launch_count(const mss_ctx* ctx);

@@ -29,8 +29,8 @@ MSS_HIT_REPEAT = 1
 
 # every symbol include/maxss.h declares
 EXPORTS = ("mss_load_genome", "mss_load_genome_device", "mss_get_info", "mss_set_frag_len", "mss_set_tune",
-           "mss_get_tune", "mss_map_reads", "mss_map_reads_device", "nw_align", "nw_align_device", "mss_sync",
-           "mss_autotune", "mss_launch_count", "mss_genome_codes", "mss_probe_pipes", "mss_free", "mss_last_error")
+           "mss_get_tune", "mss_map_reads", "mss_map_reads_device", "nw_align", "nw_align_device", "mss_map_align", "mss_sync",
+           "mss_autotune", "mss_scan_timing", "mss_scan_time_ms", "mss_launch_count", "mss_genome_codes", "mss_probe_pipes", "mss_free", "mss_last_error")
 
 HIT_DTYPE = np.dtype([("best_frag", np.int32), ("second_frag", np.int32), ("best_score", np.int32),
                       ("second_score", np.int32), ("offset", np.int64), ("strand", np.int32), ("flags", np.int32)])
@@ -91,8 +91,12 @@ def load_library(path: str = LIB_PATH):
         "mss_map_reads_device": ([P, P, P, i32, i32, ctypes.POINTER(ScoreParams), P, P], i32),
         "nw_align": ([P, P, P, i32, P, ctypes.POINTER(NwParams), P, P, i32, P], i32),
         "nw_align_device": ([P, P, P, i32, i32, P, ctypes.POINTER(NwParams), P, P, i32, P], i32),
+        "mss_map_align": ([P, P, P, i32, ctypes.POINTER(ScoreParams), ctypes.POINTER(NwParams), P, P, P, i32, P],
+                          i32),
         "mss_sync": ([P, P], i32),
         "mss_autotune": ([P, P, P, i32, i32, ctypes.POINTER(ScoreParams), i32, P], i32),
+        "mss_scan_timing": ([P, i32], i32),
+        "mss_scan_time_ms": ([P, ctypes.POINTER(ctypes.c_float)], i32),
         "mss_launch_count": ([P], i64),
         "mss_genome_codes": ([P, i64, i64, P], i32),
         "mss_probe_pipes": ([ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], i32),
@@ -241,6 +245,31 @@ def nw_align_device(g: Genome, d_reads, d_offsets, R: int, max_len: int, d_hits,
     _check(st, "nw_align_device")
 
 
+def mss_map_align(g: Genome, reads, offsets, match: int, mismatch: int, nw=(5, -4, -26, -26, 32), hits=None,
+                  alns=None, cigars=None, cigar_stride: int = 0, stream=None):
+    """Both phases, host buffers (numpy or pinned torch), one upload.  Outputs are allocated as
+    numpy arrays unless given.  Returns (hits, alns, cigar bytes [R, stride])."""
+    R = (offsets.shape[0] if isinstance(offsets, np.ndarray) else offsets.numel()) - 1
+    if cigar_stride <= 0:
+        lens = np.diff(np.asarray(offsets if isinstance(offsets, np.ndarray) else offsets.numpy()))
+        cigar_stride = int(max(16, 4 * (int(lens.max()) if R else 1) + 64))
+    hits = np.zeros(R, dtype=HIT_DTYPE) if hits is None else hits
+    alns = np.zeros(R, dtype=ALN_DTYPE) if alns is None else alns
+    cigars = np.zeros((max(R, 1), cigar_stride), dtype=np.uint8) if cigars is None else cigars
+    sp = ScoreParams(match, mismatch)
+    npar = NwParams(*nw, 0)
+    st = load_library().mss_map_align(g.handle, _host_ptr(reads), _host_ptr(offsets), R, ctypes.byref(sp),
+                                      ctypes.byref(npar), _host_ptr(hits), _host_ptr(alns), _host_ptr(cigars),
+                                      cigar_stride, _stream_ptr(stream))
+    _check(st, "mss_map_align")
+    return hits, alns, cigars
+
+
+def cigar_strings(alns, cigars) -> list:
+    """Decode CIGAR slots (numpy [R, stride] uint8) using the lengths in alns."""
+    return [bytes(cigars[i, :max(int(alns["cigar_len"][i]), 0)]).decode() for i in range(len(alns))]
+
+
 def mss_sync(g: Genome, stream=None):
     _check(load_library().mss_sync(g.handle, _stream_ptr(stream)), "mss_sync")
 
@@ -252,6 +281,16 @@ def mss_autotune(g: Genome, d_reads, d_offsets, R: int, max_len: int, match: int
                                      ctypes.byref(sp), 1 if allow_frag_len else 0, _stream_ptr(stream))
     _check(st, "mss_autotune")
     return {**mss_get_tune(g), "frag_len": g.info()["frag_len"]}
+
+
+def mss_scan_timing(g: Genome, enable: bool = True):
+    _check(load_library().mss_scan_timing(g.handle, 1 if enable else 0), "mss_scan_timing")
+
+
+def mss_scan_time_ms(g: Genome) -> float:
+    ms = ctypes.c_float()
+    _check(load_library().mss_scan_time_ms(g.handle, ctypes.byref(ms)), "mss_scan_time_ms")
+    return float(ms.value)
 
 
 def mss_launch_count(g: Genome) -> int:

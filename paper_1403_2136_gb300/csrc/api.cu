@@ -90,6 +90,7 @@ struct GraphKey {
   int64_t chunk_len;
   cudaStream_t stream;
   const void* ws[4];  // workspace pointers baked into the graph
+  bool timing;        // event nodes around the scan
   bool operator==(const GraphKey& o) const { return memcmp(this, &o, sizeof(GraphKey)) == 0; }
 };
 
@@ -109,6 +110,8 @@ struct mss_ctx {
   cudaGraphExec_t graph = nullptr;
   GraphKey gkey;
   bool have_graph = false;
+  cudaEvent_t ev_scan[2] = {nullptr, nullptr};  // optional events around the scan kernel
+  bool timing = false;
 
   void set_frag(int64_t f) {
     F = f;
@@ -260,7 +263,9 @@ mss_status enqueue_map(mss_ctx* c, const char* d_reads, const int64_t* d_offsets
     a.mm_word = a.prof_mismatch * 0x01010101u;
   }
   const int g = (int)std::max<int64_t>(1, std::min<int64_t>(grid, a.n_items));
+  if (c->timing) CK(cudaEventRecordWithFlags(c->ev_scan[0], s, cudaEventRecordExternal), "timing event");
   CK(launch_scan(cfg, a, g, smem, s), "scan kernel");
+  if (c->timing) CK(cudaEventRecordWithFlags(c->ev_scan[1], s, cudaEventRecordExternal), "timing event");
   FinalArgs f{};
   f.g2 = c->pg.g2;
   f.gm = c->pg.gm;
@@ -324,6 +329,7 @@ mss_status map_device(mss_ctx* c, const char* d_reads, const int64_t* d_offsets,
   key.ws[1] = c->order.p;
   key.ws[2] = c->partial.p;
   key.ws[3] = c->queue.p;
+  key.timing = c->timing;
   if (!(c->have_graph && c->gkey == key)) {
     if (c->graph) {
       cudaGraphExecDestroy(c->graph);
@@ -564,6 +570,32 @@ mss_status nw_align(mss_ctx* c, const char* reads, const int64_t* offsets, int32
   return read_err(c, s);
 }
 
+mss_status mss_map_align(mss_ctx* c, const char* reads, const int64_t* offsets, int32_t R,
+                         const mss_score_params* sp, const mss_nw_params* np, mss_hit* hits, mss_aln* alns, char* cig,
+                         int32_t stride, void* stream) {
+  if (check_ctx(c)) return MSS_EINVAL;
+  mss_status st = check_nw(np, stride);
+  if (st) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  int32_t ml = 0;
+  st = stage_reads(c, reads, offsets, R, &ml, s);
+  if (st || R == 0) return st;
+  if (!hits || !alns || !cig) return fail(MSS_EINVAL, "null buffer");
+  CK(c->h_hits.ensure(sizeof(mss_hit) * (size_t)R), "staging");
+  CK(c->h_alns.ensure(sizeof(mss_aln) * (size_t)R), "staging");
+  CK(c->h_cigars.ensure((size_t)R * (size_t)stride), "staging");
+  st = map_device(c, (const char*)c->h_reads.p, (const int64_t*)c->h_offsets.p, R, ml, sp, (mss_hit*)c->h_hits.p, s,
+                  true);
+  if (st) return st;
+  st = nw_device(c, (const char*)c->h_reads.p, (const int64_t*)c->h_offsets.p, R, ml, (const mss_hit*)c->h_hits.p, np,
+                 (mss_aln*)c->h_alns.p, (char*)c->h_cigars.p, stride, s);
+  if (st) return st;
+  CK(cudaMemcpyAsync(hits, c->h_hits.p, sizeof(mss_hit) * (size_t)R, cudaMemcpyDeviceToHost, s), "hits download");
+  CK(cudaMemcpyAsync(alns, c->h_alns.p, sizeof(mss_aln) * (size_t)R, cudaMemcpyDeviceToHost, s), "alns download");
+  CK(cudaMemcpyAsync(cig, c->h_cigars.p, (size_t)R * (size_t)stride, cudaMemcpyDeviceToHost, s), "cigar download");
+  return read_err(c, s);
+}
+
 mss_status mss_sync(mss_ctx* c, void* stream) {
   if (check_ctx(c)) return MSS_EINVAL;
   return read_err(c, (cudaStream_t)stream);
@@ -625,6 +657,24 @@ mss_status mss_autotune(mss_ctx* c, const char* d_reads, const int64_t* d_offset
   return read_err(c, s);
 }
 
+mss_status mss_scan_timing(mss_ctx* c, int32_t enable) {
+  if (check_ctx(c)) return MSS_EINVAL;
+  if (enable && !c->ev_scan[0]) {
+    CK(cudaEventCreate(&c->ev_scan[0]), "event create");
+    CK(cudaEventCreate(&c->ev_scan[1]), "event create");
+  }
+  c->timing = enable != 0;
+  return MSS_OK;
+}
+
+mss_status mss_scan_time_ms(mss_ctx* c, float* ms) {
+  if (check_ctx(c) || !ms) return fail(MSS_EINVAL, "null argument");
+  if (!c->ev_scan[0]) return fail(MSS_ESTATE, "scan timing was never enabled");
+  CK(cudaEventSynchronize(c->ev_scan[1]), "event synchronize");
+  CK(cudaEventElapsedTime(ms, c->ev_scan[0], c->ev_scan[1]), "event elapsed time");
+  return MSS_OK;
+}
+
 int64_t mss_launch_count(const mss_ctx* c) { return c ? c->launches : -1; }
 
 mss_status mss_genome_codes(const mss_ctx* c, int64_t start, int64_t n, uint8_t* out) {
@@ -650,6 +700,8 @@ mss_status mss_probe_pipes(double* rates3, double* clk_mhz) {
 void mss_free(mss_ctx* c) {
   if (!c) return;
   if (c->graph) cudaGraphExecDestroy(c->graph);
+  for (cudaEvent_t e : c->ev_scan)
+    if (e) cudaEventDestroy(e);
   if (c->pg.g2) cudaFree(c->pg.g2);
   if (c->pg.gm) cudaFree(c->pg.gm);
   if (c->d_err) cudaFree(c->d_err);
