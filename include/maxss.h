@@ -170,6 +170,22 @@ MSS_API mss_status nw_align_device(mss_ctx* ctx, const char* d_reads, const int6
                            char* d_cigar_buf, int32_t cigar_stride, void* stream);
 
 /*
+ * nw_align_device with no allocation of any kind (the paper has no counterpart; this is a
+ * deployment interface).  For callers that cannot call cudaMalloc: code running inside CUDA
+ * stream capture, latency-critical serving loops, and processes whose device memory belongs
+ * to a pool allocator.  Same arguments and results as nw_align_device; the traceback scratch
+ * is a fixed 4 MiB array in the library's device image (held by every GPU that loads the
+ * library until exit), so long reads get fewer concurrent traceback slots, never a failure,
+ * as long as one slot fits (always true up to MSS_MAX_READ_LEN and band 63; otherwise
+ * MSS_EINVAL).  The array's device address is looked up on the first call on each device:
+ * make that first call outside any stream capture.  All calls share the array, so calls
+ * that may run concurrently on the GPU race and must be ordered by the caller.
+ */
+MSS_API mss_status nw_align_device_noalloc(mss_ctx* ctx, const char* d_reads, const int64_t* d_offsets, int32_t R,
+                                           int32_t max_len, const mss_hit* d_hits, const mss_nw_params* np,
+                                           mss_aln* d_out, char* d_cigar_buf, int32_t cigar_stride, void* stream);
+
+/*
  * Both phases for R reads with host buffers and one upload: reads/offsets as in
  * mss_map_reads; hits[R], alns[R] and cigar_buf (R slots of cigar_stride bytes) receive the
  * results.  Synchronous.  This is the end-to-end call (host -> device -> host).

@@ -29,7 +29,7 @@ MSS_HIT_REPEAT = 1
 
 # every symbol include/maxss.h declares
 EXPORTS = ("mss_load_genome", "mss_load_genome_device", "mss_get_info", "mss_set_frag_len", "mss_set_tune",
-           "mss_get_tune", "mss_map_reads", "mss_map_reads_device", "nw_align", "nw_align_device", "mss_map_align", "mss_sync",
+           "mss_get_tune", "mss_map_reads", "mss_map_reads_device", "nw_align", "nw_align_device", "nw_align_device_noalloc", "mss_map_align", "mss_sync",
            "mss_autotune", "mss_scan_timing", "mss_scan_time_ms", "mss_launch_count", "mss_genome_codes", "mss_probe_pipes", "mss_free", "mss_last_error")
 
 HIT_DTYPE = np.dtype([("best_frag", np.int32), ("second_frag", np.int32), ("best_score", np.int32),
@@ -91,6 +91,7 @@ def load_library(path: str = LIB_PATH):
         "mss_map_reads_device": ([P, P, P, i32, i32, ctypes.POINTER(ScoreParams), P, P], i32),
         "nw_align": ([P, P, P, i32, P, ctypes.POINTER(NwParams), P, P, i32, P], i32),
         "nw_align_device": ([P, P, P, i32, i32, P, ctypes.POINTER(NwParams), P, P, i32, P], i32),
+        "nw_align_device_noalloc": ([P, P, P, i32, i32, P, ctypes.POINTER(NwParams), P, P, i32, P], i32),
         "mss_map_align": ([P, P, P, i32, ctypes.POINTER(ScoreParams), ctypes.POINTER(NwParams), P, P, P, i32, P],
                           i32),
         "mss_sync": ([P, P], i32),

@@ -435,6 +435,24 @@ mss_status stage_reads(mss_ctx* c, const char* reads, const int64_t* offsets, in
 
 }  // namespace
 
+namespace mss {
+
+bool ctx_view(mss_ctx* c, CtxView* v) {
+  if (!c || !v) return false;
+  v->g2 = c->pg.g2;
+  v->gm = c->pg.gm;
+  v->G = c->G;
+  v->max_len = c->max_len;
+  v->num_sms = c->num_sms;
+  v->d_err = c->d_err;
+  v->launches = &c->launches;
+  return true;
+}
+
+int32_t set_error(int32_t st, const char* msg) { return fail(st, "%s", msg); }
+
+}  // namespace mss
+
 extern "C" {
 
 mss_status mss_load_genome(mss_ctx** out, const char* seq, int64_t len, const mss_genome_params* p, void* stream) {

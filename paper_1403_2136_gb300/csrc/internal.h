@@ -113,3 +113,23 @@ cudaError_t launch_nw(const NwArgs& a, int grid_warps, cudaStream_t s);
 cudaError_t probe_pipes(double* rates3, double* clk_mhz);
 
 }  // namespace mss
+
+typedef struct mss_ctx mss_ctx;
+
+namespace mss {
+
+// Read-only view of a context for entry points defined outside api.cu.
+struct CtxView {
+  const uint32_t* g2;
+  const uint32_t* gm;
+  int64_t G;
+  int32_t max_len;
+  int32_t num_sms;
+  int32_t* d_err;
+  int64_t* launches;
+};
+bool ctx_view(mss_ctx* c, CtxView* v);
+// Record the thread-local message returned by mss_last_error() and return st.
+int32_t set_error(int32_t st, const char* msg);
+
+}  // namespace mss
