@@ -117,12 +117,13 @@ typedef struct {
   int32_t variant;       /* 0: int16 DPX add-max-relu (any scores); 1: f16 add-relu on the FMA
                             pipe + DPX running max (exact when max_read_len*match <= 2048 and the
                             scores are small integers); -1 = pick automatically */
-  int32_t pairs;         /* diagonal pairs per thread: 4 or 8 (0 = default) */
-  int32_t queries;       /* query sequences (read strands) per CTA: 4 or 8 (0 = default) */
+  int32_t pairs;         /* diagonal pairs per thread: 4 or 8 (0 = default 8) */
+  int32_t queries;       /* query sequences (read strands) per CTA: 4 or 8 (0 = default: 4 with
+                            8 pairs, else 8); 8 pairs with 8 queries is not built */
   int32_t ctas_per_sm;   /* persistent CTAs per SM (0 = occupancy maximum) */
   int32_t min_items_per_cta; /* split the genome into chunks until there are this many work
                                 items per CTA (0 = default 4) */
-  int32_t reserved;
+  int32_t reserved;      /* must be 0 */
 } mss_tune;
 
 /* Load and 2-bit pack a genome (host ASCII, length len >= 1).  Creates *out. */

@@ -104,7 +104,7 @@ struct mss_ctx {
   int32_t max_len = MSS_MAX_READ_LEN;
   int32_t* d_err = nullptr;
   int64_t launches = 0;
-  mss_tune tune{-1, 0, 0, 0, 0, 0};
+  mss_tune tune{-1, 0, 0, 0, 0, 0};  // automatic
   DevBuf hist, order, partial, queue, nw_scratch;
   DevBuf h_reads, h_offsets, h_hits, h_alns, h_cigars;  // staging for the host-pointer calls
   cudaGraphExec_t graph = nullptr;
@@ -192,12 +192,15 @@ mss_status resolve_config(const mss_ctx* c, int32_t max_len, const mss_score_par
   if (variant == 1 && !exact16)
     return fail(MSS_EINVAL, "f16 scan variant is not exact for these scores / read lengths");
   cfg->variant = variant;
-  cfg->pairs = t.pairs ? t.pairs : 4;
-  cfg->queries = t.queries ? t.queries : 8;
+  cfg->pairs = t.pairs ? t.pairs : 8;
+  cfg->queries = t.queries ? t.queries : (cfg->pairs == 8 ? 4 : 8);
   cfg->threads = 256;
+  cfg->max_len = max_len;
   *slots = scan_ring_slots(*cfg, c->F);
   *smem = scan_smem_bytes(*cfg, max_len, *slots);
-  if (*smem == 0) return fail(MSS_EINVAL, "unsupported scan configuration (pairs %d, queries %d)", cfg->pairs, cfg->queries);
+  if (*smem == 0)
+    return fail(MSS_EINVAL, "unsupported scan configuration (pairs %d, queries %d, max_len %d)", cfg->pairs,
+                cfg->queries, max_len);
   int per_sm = 0;
   CK(scan_max_ctas_per_sm(*cfg, *smem, &per_sm), "scan occupancy");
   if (per_sm < 1) return fail(MSS_EINVAL, "scan configuration does not fit on an SM");
@@ -517,6 +520,7 @@ mss_status mss_set_tune(mss_ctx* c, const mss_tune* t) {
   if (t->variant < -1 || t->variant > 1) return fail(MSS_EINVAL, "variant must be -1, 0 or 1");
   if (t->pairs != 0 && t->pairs != 4 && t->pairs != 8) return fail(MSS_EINVAL, "pairs must be 4 or 8");
   if (t->queries != 0 && t->queries != 4 && t->queries != 8) return fail(MSS_EINVAL, "queries must be 4 or 8");
+  if (t->reserved != 0) return fail(MSS_EINVAL, "mss_tune.reserved must be 0");
   if ((t->pairs == 8 ? 8 : 4) == 8 && t->queries == 8) return fail(MSS_EINVAL, "pairs 8 with queries 8 is not built");
   if (t->pairs == 8 && t->queries == 0) {
     mss_tune u = *t;
@@ -633,7 +637,8 @@ mss_status mss_autotune(mss_ctx* c, const char* d_reads, const int64_t* d_offset
   for (int v = exact16 ? 1 : 0; v >= 0; --v)
     for (int pq = 0; pq < 3; ++pq)
       for (int cps : {0, 1}) {
-        mss_tune t{v, pq == 1 ? 8 : 4, pq == 1 ? 4 : (pq == 2 ? 4 : 8), cps, 0, 0};
+        const int pairs = pq == 1 ? 8 : 4, queries = pq == 1 ? 4 : (pq == 2 ? 4 : 8);
+        mss_tune t{v, pairs, queries, cps, 0, 0};
         cands.push_back(t);
       }
   std::vector<int64_t> frags = {c->F};

@@ -54,10 +54,18 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
                : "memory");
 }
 
-// Bounded wait on an mbarrier phase: returns false after max_iter unsuccessful polls.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t max_iter) {
-  uint32_t addr = smem_u32(bar);
-  for (uint32_t it = 0; it < max_iter; ++it) {
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait on an mbarrier phase: returns false if the phase has not completed after
+// limit_ns nanoseconds of polling (a poll takes about 25 ns).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+  const uint32_t addr = smem_u32(bar);
+  uint64_t t0 = 0;
+  for (uint32_t it = 0;; ++it) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
@@ -67,8 +75,12 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32
         : "r"(addr), "r"(parity)
         : "memory");
     if (done) return true;
+    if ((it & 255u) == 0) {  // read the clock every 256 polls
+      const uint64_t now = global_ns();
+      if (it == 0) t0 = now;
+      else if (now - t0 > limit_ns) return false;
+    }
   }
-  return false;
 }
 
 // One-dimensional bulk copy global -> shared through the TMA unit, completing on an mbarrier.

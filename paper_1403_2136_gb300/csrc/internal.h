@@ -15,7 +15,7 @@ enum : int32_t {
 
 // Genome tiles: the largest tile a scan variant uses and the extra positions past the last
 // fragment that a tile may read; the packed genome is allocated (zero = N) to cover them.
-constexpr int64_t kMaxTileDiags = 4096;
+constexpr int64_t kMaxTileDiags = 4096;  // largest NT * 2D of any scan variant
 constexpr int64_t kGenomeTailPad = kMaxTileDiags + 2432 + 512;
 
 struct PackedGenome {
@@ -39,6 +39,7 @@ struct ScanConfig {
   int pairs;    // D
   int queries;  // RQ
   int threads;  // NT
+  int max_len;  // longest read of the call (selects the selector-row size)
 };
 
 struct ScanArgs {

@@ -33,12 +33,14 @@
 
 namespace mss {
 
-template <int D, int NT>
+// D lane pairs per thread, NT threads, reads up to MAXL bases (selector rows sized for it)
+template <int D, int NT, int MAXL>
 struct ScanGeo {
   static constexpr int kSpan = 2 * D;                                     // diagonals per thread
   static constexpr int kTile = NT * kSpan;                                // diagonals per tile
-  static constexpr int kSelCols = (kTile + MSS_MAX_READ_LEN + 2 * D + kSpan - 1) / kSpan;
-  static constexpr int kRawPos = ((kTile + MSS_MAX_READ_LEN + 4 * D + 16 + 127) / 128) * 128;
+  static constexpr int kSelCols = (kTile + MAXL + 2 * D + kSpan - 1) / kSpan;
+  static constexpr int kSelWords = kSpan * kSelCols;                      // one selector buffer
+  static constexpr int kRawPos = ((kTile + MAXL + 4 * D + 16 + 127) / 128) * 128;
   static constexpr uint32_t kRawG2Bytes = kRawPos / 4;
   static constexpr uint32_t kRawGmBytes = kRawPos / 8;
   static constexpr uint32_t kRawBytes = kRawG2Bytes + kRawGmBytes;
@@ -48,14 +50,14 @@ struct SmemLayout {
   size_t prof, sel, raw, ring, top, mbar, misc, total;
 };
 
-template <int D, int RQ, int NT>
+template <int D, int RQ, int NT, int MAXL>
 __host__ __device__ inline SmemLayout scan_layout(int32_t max_len, int32_t ring_slots) {
-  using Geo = ScanGeo<D, NT>;
+  using Geo = ScanGeo<D, NT, MAXL>;
   SmemLayout L;
   size_t mpad_max = (size_t)((max_len + 7) & ~7);
   L.prof = 0;
-  L.sel = L.prof + mpad_max * RQ * 4;
-  L.raw = L.sel + (size_t)Geo::kSpan * Geo::kSelCols * 4;
+  L.sel = L.prof + (mpad_max + 1) * RQ * 4;  // one padding row: the scan reads one row ahead
+  L.raw = L.sel + 2 * (size_t)Geo::kSelWords * 4;  // two selector buffers (tile t and t+1)
   L.raw = (L.raw + 127) & ~(size_t)127;
   L.ring = L.raw + 2 * (size_t)Geo::kRawBytes;
   L.top = L.ring + (size_t)(RQ / 2) * ring_slots * 4;
@@ -99,9 +101,9 @@ __device__ __forceinline__ int32_t lane_value(uint32_t bits16) {
   return (int32_t)(int16_t)(bits16 & 0xFFFFu);
 }
 
-template <bool F16, int D, int RQ, int NT>
-__global__ void __launch_bounds__(NT, 2) k_scan(ScanArgs a) {
-  using Geo = ScanGeo<D, NT>;
+template <bool F16, int D, int RQ, int NT, int MAXL, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_scan(ScanArgs a) {
+  using Geo = ScanGeo<D, NT, MAXL>;
   constexpr int RG = RQ / 2;
   constexpr int SPAN = Geo::kSpan;
   constexpr int TILE = Geo::kTile;
@@ -111,9 +113,9 @@ __global__ void __launch_bounds__(NT, 2) k_scan(ScanArgs a) {
   static_assert(RG <= 4, "read lengths occupy 16 bytes of the misc area");
 
   extern __shared__ __align__(128) uint8_t smem[];
-  const SmemLayout L = scan_layout<D, RQ, NT>(a.max_len, a.ring_slots);
+  const SmemLayout L = scan_layout<D, RQ, NT, MAXL>(a.max_len, a.ring_slots);
   uint32_t* prof = reinterpret_cast<uint32_t*>(smem + L.prof);
-  uint32_t* sel = reinterpret_cast<uint32_t*>(smem + L.sel);
+  uint32_t* const sel_base = reinterpret_cast<uint32_t*>(smem + L.sel);
   uint8_t* raw = smem + L.raw;
   int32_t* ring = reinterpret_cast<int32_t*>(smem + L.ring);
   Top2* top = reinterpret_cast<Top2*>(smem + L.top);
@@ -133,7 +135,9 @@ __global__ void __launch_bounds__(NT, 2) k_scan(ScanArgs a) {
   }
   __syncthreads();
   uint32_t parity[2] = {0u, 0u};
+  int32_t armed[2] = {-1, -1};  // thread 0: parity of the last phase armed on each mbarrier
   bool timed_out = false;
+  constexpr uint64_t kWaitLimitNs = 2000000000ull;  // a tile's copy completes in microseconds
 
   for (;;) {
     if (tid == 0) *s_item = atomicAdd(a.queue, 1);
@@ -188,11 +192,18 @@ __global__ void __launch_bounds__(NT, 2) k_scan(ScanArgs a) {
     const int32_t f_lo = (int32_t)(c0 / a.F);
     const int32_t f_end = (int32_t)((c1 - 1) / a.F) + 1;
     int32_t fold_next = f_lo;
+    // fragment of the current tile start and of this thread's first diagonal, with remainders,
+    // advanced by TILE per tile without dividing again
+    const int64_t tile_step_q = TILE / a.F, tile_step_rem = TILE % a.F;
+    int64_t tile_frag = c0 / a.F, tile_rem = c0 - tile_frag * a.F;
+    int64_t th_frag = (c0 + (int64_t)tid * SPAN) / a.F;
+    int64_t th_rem = c0 + (int64_t)tid * SPAN - th_frag * a.F;
 
     auto issue = [&](int t, int buf) {
       const int64_t ts = c0 + (int64_t)t * TILE;
       uint8_t* dst = raw + buf * Geo::kRawBytes;
       fence_proxy_async_smem();
+      armed[buf] = (int32_t)parity[buf];
       mbar_arrive_expect_tx(&mbar[buf], Geo::kRawBytes);
       tma_load_1d(dst, reinterpret_cast<const uint8_t*>(a.g2) + ts / 4, Geo::kRawG2Bytes, &mbar[buf]);
       tma_load_1d(dst + Geo::kRawG2Bytes, reinterpret_cast<const uint8_t*>(a.gm) + ts / 8, Geo::kRawGmBytes,
@@ -219,8 +230,11 @@ __global__ void __launch_bounds__(NT, 2) k_scan(ScanArgs a) {
 
     for (int t = 0; t < ntiles; ++t) {
       const int buf = t & 1;
+      // selector buffer of this tile: written by the expansion below, read by the scan; the
+      // other buffer may still be read by warps finishing tile t-1 (one barrier per tile)
+      uint32_t* const sel = sel_base + buf * Geo::kSelWords;
       if (tid == 0 && t + 1 < ntiles) issue(t + 1, buf ^ 1);
-      if (!mbar_wait(&mbar[buf], parity[buf], 1u << 20)) timed_out = true;
+      if (!mbar_wait(&mbar[buf], parity[buf], kWaitLimitNs)) timed_out = true;
       parity[buf] ^= 1u;
 
       // expand the staged 2-bit genome into selector words: sel[row * W + col] is the
@@ -228,23 +242,26 @@ __global__ void __launch_bounds__(NT, 2) k_scan(ScanArgs a) {
       {
         const uint32_t* rg2 = reinterpret_cast<const uint32_t*>(raw + buf * Geo::kRawBytes);
         const uint32_t* rgm = reinterpret_cast<const uint32_t*>(raw + buf * Geo::kRawBytes + Geo::kRawG2Bytes);
+        // one selector column per thread: positions P .. P + SPAN - 1 and their partners at
+        // +D; their 2-bit codes and valid bits fit in two aligned words each
         const int ncols = (TILE + mpad + D + SPAN - 1) / SPAN;
-        for (int e = tid; e < SPAN * ncols; e += NT) {
-          const int row = e / ncols, col = e - row * ncols;
-          const int p = col * SPAN + row;
-          const uint32_t q1 = (rg2[p >> 4] >> ((p & 15) * 2)) & 3u;
-          const uint32_t v1 = (rgm[p >> 5] >> (p & 31)) & 1u;
-          const int p2 = p + D;
-          const uint32_t q2 = (rg2[p2 >> 4] >> ((p2 & 15) * 2)) & 3u;
-          const uint32_t v2 = (rgm[p2 >> 5] >> (p2 & 31)) & 1u;
-          sel[row * W + col] = make_sel<F16>(v1 ? q1 : 4u, v2 ? q2 : 4u);
+        for (int col = tid; col < ncols; col += NT) {
+          const int P = col * SPAN;
+          const uint64_t gw = ((((uint64_t)rg2[(P >> 4) + 1]) << 32) | rg2[P >> 4]) >> (2 * (P & 15));
+          const uint64_t vw = ((((uint64_t)rgm[(P >> 5) + 1]) << 32) | rgm[P >> 5]) >> (P & 31);
+#pragma unroll
+          for (int r = 0; r < SPAN; ++r) {
+            const uint32_t c1 = ((vw >> r) & 1u) ? (uint32_t)((gw >> (2 * r)) & 3u) : 4u;
+            const uint32_t c2 = ((vw >> (r + D)) & 1u) ? (uint32_t)((gw >> (2 * (r + D))) & 3u) : 4u;
+            sel[r * W + col] = make_sel<F16>(c1, c2);
+          }
         }
       }
       __syncthreads();
 
       const int64_t ts = c0 + (int64_t)t * TILE;
       {
-        const int64_t tf = ts / a.F;
+        const int64_t tf = tile_frag;  // = ts / F
         const int32_t done = (int32_t)(tf < (int64_t)f_end ? tf : (int64_t)f_end);  // fragments < done are complete
         if (warp < RG && done > fold_next) fold(warp, fold_next, done);
         fold_next = max(fold_next, done);
@@ -254,52 +271,72 @@ __global__ void __launch_bounds__(NT, 2) k_scan(ScanArgs a) {
       uint32_t win[D];
 #pragma unroll
       for (int j = 0; j < D; ++j) win[j] = sel[j * W + tid];
-      uint32_t H[RQ][D], Ha[RQ][D], M[RQ][D];
+      // H: latest Kadane value per lane pair; M: running maximum.  Each pair folds two new H
+      // values into M with one 3-input max every second step; pairs with odd j fold on even
+      // steps and pairs with even j on odd steps, so every step carries the same mix of
+      // integer-pipe (PRMT, max) and FMA-pipe (H update) instructions.
+      uint32_t H[RQ][D], M[RQ][D];
 #pragma unroll
       for (int q = 0; q < RQ; ++q)
 #pragma unroll
-        for (int j = 0; j < D; ++j) H[q][j] = 0u, Ha[q][j] = 0u, M[q][j] = 0u;
+        for (int j = 0; j < D; ++j) H[q][j] = 0u, M[q][j] = 0u;
+
+      // profile row of the next step, loaded one step ahead (hides the shared-memory latency,
+      // also across block boundaries; the row after the last is padding)
+      uint4 pnext[RQ / 4];
+#pragma unroll
+      for (int v = 0; v < RQ / 4; ++v) pnext[v] = reinterpret_cast<const uint4*>(prof)[v];
 
       for (int k0 = 0; k0 < mpad; k0 += D) {
         // positions entering the window during this block: p = tid*SPAN + k0 + u + D, u < D,
         // all in one selector row band and one column
         const int kk = k0 + D;
         const uint32_t* sp = sel + (kk % SPAN) * W + tid + kk / SPAN;
-        const uint4* pp = reinterpret_cast<const uint4*>(prof + k0 * RQ);
+        const uint4* pp = reinterpret_cast<const uint4*>(prof + (k0 + 1) * RQ);
 #pragma unroll
         for (int u = 0; u < D; ++u) {
           uint32_t pw[RQ];
 #pragma unroll
           for (int v = 0; v < RQ / 4; ++v) {
-            const uint4 x = pp[u * (RQ / 4) + v];
-            pw[4 * v + 0] = x.x;
-            pw[4 * v + 1] = x.y;
-            pw[4 * v + 2] = x.z;
-            pw[4 * v + 3] = x.w;
+            pw[4 * v + 0] = pnext[v].x;
+            pw[4 * v + 1] = pnext[v].y;
+            pw[4 * v + 2] = pnext[v].z;
+            pw[4 * v + 3] = pnext[v].w;
           }
+#pragma unroll
+          for (int v = 0; v < RQ / 4; ++v) pnext[v] = pp[u * (RQ / 4) + v];
 #pragma unroll
           for (int q = 0; q < RQ; ++q) {
 #pragma unroll
             for (int j = 0; j < D; ++j) {
               const uint32_t s = prmt(pw[q], mmw, win[(j + u) % D]);
-              if ((u & 1) == 0) {
-                Ha[q][j] = kadane_step<F16>(H[q][j], s);
-              } else {
-                const uint32_t h = kadane_step<F16>(Ha[q][j], s);
-                M[q][j] = __vimax3_s16x2(M[q][j], Ha[q][j], h);
-                H[q][j] = h;
-              }
+              const uint32_t h = kadane_step<F16>(H[q][j], s);
+              if ((u & 1) != (j & 1)) M[q][j] = __vimax3_s16x2(M[q][j], H[q][j], h);
+              H[q][j] = h;
             }
           }
           win[u] = sp[u * W];
         }
       }
+      // mpad is a multiple of D (even): the last step is odd, so pairs with odd j hold one
+      // value not yet folded
+#pragma unroll
+      for (int q = 0; q < RQ; ++q)
+#pragma unroll
+        for (int j = 1; j < D; j += 2) M[q][j] = __vimax3_s16x2(M[q][j], H[q][j], 0u);
 
       // ---- per-fragment maxima of this thread's 2D diagonals
       const int64_t ds = ts + (int64_t)tid * SPAN;
-      const int32_t fA = (int32_t)(ds / a.F);
-      const int64_t bnd = (int64_t)(fA + 1) * a.F;
-      const bool split = ds + SPAN > bnd;
+      const int32_t fA = (int32_t)th_frag;          // = ds / F
+      const int64_t bnd = ds - th_rem + a.F;        // start of fragment fA + 1
+      const bool split = th_rem + SPAN > a.F;
+      // advance the per-tile and per-thread fragment positions by one tile
+      tile_rem += tile_step_rem;
+      tile_frag += tile_step_q + (tile_rem >= a.F ? 1 : 0);
+      if (tile_rem >= a.F) tile_rem -= a.F;
+      th_rem += tile_step_rem;
+      th_frag += tile_step_q + (th_rem >= a.F ? 1 : 0);
+      if (th_rem >= a.F) th_rem -= a.F;
       const int32_t fA0 = __shfl_sync(0xffffffffu, fA, 0);
       const bool uni = __all_sync(0xffffffffu, (fA == fA0) && !split);
       uint32_t maskA[D];
@@ -327,8 +364,8 @@ __global__ void __launch_bounds__(NT, 2) k_scan(ScanArgs a) {
           if (vB > 0) atomicMax(&ring[r * S + (int)((fA + 1) % S)], vB);
         }
       }
-      __syncthreads();
     }
+    __syncthreads();  // every fragment slot of the last tile is final
 
     if (warp < RG && f_end > fold_next) fold(warp, fold_next, f_end);
     __syncthreads();
@@ -340,25 +377,44 @@ __global__ void __launch_bounds__(NT, 2) k_scan(ScanArgs a) {
     // the next item rewrites the profile, ring and summaries only after the barrier at its top
   }
   if (timed_out) atomicOr(a.err, ERR_TIMEOUT);
+  // never leave with a bulk copy in flight: thread 0 waits (bounded) for the last phase it
+  // armed on each buffer; phases that were already waited on return at once
+  if (tid == 0) {
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+      if (armed[b] >= 0 && !mbar_wait(&mbar[b], (uint32_t)armed[b], kWaitLimitNs)) atomicOr(a.err, ERR_TIMEOUT);
+  }
 }
 
 // ---------------------------------------------------------------- host side of the scan
-#define MSS_SCAN_VARIANTS(X) \
-  X(false, 4, 8, 256)        \
-  X(true, 4, 8, 256)         \
-  X(false, 8, 4, 256)        \
-  X(true, 8, 4, 256)         \
-  X(false, 4, 4, 256)        \
-  X(true, 4, 4, 256)
+// (f16, D, RQ, NT, MAXL, min CTAs per SM)
+#define MSS_SCAN_VARIANTS(X)     \
+  X(false, 4, 8, 256, 512, 2)    \
+  X(true, 4, 8, 256, 512, 2)     \
+  X(false, 8, 4, 256, 512, 2)    \
+  X(true, 8, 4, 256, 512, 2)     \
+  X(false, 4, 4, 256, 512, 2)    \
+  X(true, 4, 4, 256, 512, 2)     \
+  X(false, 4, 8, 256, 2432, 2)   \
+  X(true, 4, 8, 256, 2432, 2)    \
+  X(false, 8, 4, 256, 2432, 2)   \
+  X(true, 8, 4, 256, 2432, 2)    \
+  X(false, 4, 4, 256, 2432, 2)   \
+  X(true, 4, 4, 256, 2432, 2)
 
-template <bool F16, int D, int RQ, int NT>
+// reads up to 512 bases use selector rows sized for 512 (less shared memory per CTA)
+static int maxl_of(int32_t max_len) { return max_len <= 512 ? 512 : 2432; }
+
+template <bool F16, int D, int RQ, int NT, int MAXL, int MINB>
 static const void* scan_fn() {
-  return reinterpret_cast<const void*>(&k_scan<F16, D, RQ, NT>);
+  return reinterpret_cast<const void*>(&k_scan<F16, D, RQ, NT, MAXL, MINB>);
 }
 
 static const void* pick_scan(const ScanConfig& c) {
-#define X(f, d, rq, nt) \
-  if (c.variant == (f ? 1 : 0) && c.pairs == d && c.queries == rq && c.threads == nt) return scan_fn<f, d, rq, nt>();
+  const int ml = maxl_of(c.max_len);
+#define X(f, d, rq, nt, mx, mb)                                                                   \
+  if (c.variant == (f ? 1 : 0) && c.pairs == d && c.queries == rq && c.threads == nt && ml == mx) \
+    return scan_fn<f, d, rq, nt, mx, mb>();
   MSS_SCAN_VARIANTS(X)
 #undef X
   return nullptr;
@@ -367,8 +423,10 @@ static const void* pick_scan(const ScanConfig& c) {
 int64_t scan_tile_diags(const ScanConfig& c) { return (int64_t)c.threads * 2 * c.pairs; }
 
 size_t scan_smem_bytes(const ScanConfig& c, int32_t max_len, int32_t ring_slots) {
-#define X(f, d, rq, nt) \
-  if (c.pairs == d && c.queries == rq && c.threads == nt) return scan_layout<d, rq, nt>(max_len, ring_slots).total;
+  const int ml = maxl_of(max_len);
+#define X(f, d, rq, nt, mx, mb)                                                    \
+  if (c.pairs == d && c.queries == rq && c.threads == nt && ml == mx)              \
+    return scan_layout<d, rq, nt, mx>(max_len, ring_slots).total;
   MSS_SCAN_VARIANTS(X)
 #undef X
   return 0;
