@@ -228,6 +228,63 @@ MSS_API mss_status mss_genome_codes(const mss_ctx* ctx, int64_t start, int64_t n
  */
 MSS_API mss_status mss_probe_pipes(double* rates3, double* clk_mhz);
 
+/* ==========================================================================================
+ * Learned fragment proposal (a step added to the method; the paper has none).  A small 1-D
+ * CNN (one-hot bases -> 4 x conv1d(128 channels, kernel 7, "same", ReLU) -> max over
+ * positions -> L2 norm; BF16 weights, FP32 accumulation) embeds reads and genome fragments.
+ * The dot product ranks fragments per read (maximum over the read's two strands); the exact
+ * scan then runs only on the top K fragments, and reads whose best proposal score is below a
+ * threshold fall back to the exhaustive scan.  Trained on labels produced by the exhaustive
+ * scan (softmax cross-entropy of the true best fragment against the other candidates,
+ * AdamW on FP32 master weights).
+ * ========================================================================================== */
+typedef struct mss_prop mss_prop;
+
+/* Create a model with deterministic random weights (uniform(+-sqrt(6/fan_in)), biases 0.01). */
+MSS_API mss_status mss_prop_create(mss_prop** out, uint64_t seed, void* stream);
+MSS_API void mss_prop_free(mss_prop* p);
+/* Number of parameters and the flat fp32 layout: W1 [7][4][128], b1 [128], then for layers
+   2..4: W [7][128 in][128 out], b [128].  get/set copy host <-> device. */
+MSS_API int64_t mss_prop_param_count(void);
+MSS_API mss_status mss_prop_get_params(const mss_prop* p, float* host, int64_t n);
+MSS_API mss_status mss_prop_set_params(mss_prop* p, const float* host, int64_t n);
+/* Input codes for the network (device buffers, codes 0..3 = ACGT, 4 = N/padding, row stride
+   ld): reads (d_idx selects reads, d_strand 1 = reverse complement; both may be NULL) and
+   genome windows [start, start + len). */
+MSS_API mss_status mss_prop_read_codes(mss_prop* p, const char* d_reads, const int64_t* d_offsets,
+                                       const int32_t* d_idx, const int8_t* d_strand, int32_t n, int32_t ld,
+                                       uint8_t* d_codes, int32_t* d_lens, void* stream);
+MSS_API mss_status mss_prop_window_codes(mss_prop* p, const mss_ctx* ctx, const int64_t* d_starts, int32_t n,
+                                         int32_t len, int32_t ld, uint8_t* d_codes, int32_t* d_lens, void* stream);
+/* Embeddings of n code sequences (lengths <= maxlen <= ld) into d_emb [n][128] (fp32). */
+MSS_API mss_status mss_prop_embed_device(mss_prop* p, const uint8_t* d_codes, const int32_t* d_lens, int32_t ld,
+                                         int32_t n, int32_t maxlen, float* d_emb, void* stream);
+/* Parameter gradient (d_grad, mss_prop_param_count() floats) of sum_i <d_demb[i], emb_i>. */
+MSS_API mss_status mss_prop_grad_device(mss_prop* p, const uint8_t* d_codes, const int32_t* d_lens, int32_t ld,
+                                        int32_t n, int32_t maxlen, const float* d_demb, float* d_grad, void* stream);
+/* One training step: B read sequences (on their labelled strand) against C candidate
+   fragment windows; label[i] = index of read i's best fragment among the candidates; loss =
+   mean softmax cross-entropy of <e_read, e_cand> / temperature.  loss_out (host) optional. */
+MSS_API mss_status mss_prop_train_step(mss_prop* p, const uint8_t* d_rcodes, const int32_t* d_rlens, int32_t ld_r,
+                                       int32_t B, int32_t maxlen_r, const uint8_t* d_ccodes, const int32_t* d_clens,
+                                       int32_t ld_c, int32_t C, int32_t maxlen_c, const int32_t* d_labels, float lr,
+                                       float temperature, float weight_decay, float* loss_out, void* stream);
+/* Embed every fragment window [fF, fF + F + max_read_len - 1) of the context's genome. */
+MSS_API mss_status mss_prop_build_index(mss_prop* p, mss_ctx* ctx, int32_t max_read_len, void* stream);
+/* Proposal + exact rescoring: per read the top K fragments by embedding score (ties -> lower
+   fragment), the exact scan of those K (both strands), and best / second among them; reads
+   whose best proposal score is below tau are mapped by the exhaustive scan instead.  Optional
+   outputs: d_cand [R][K] candidate fragments, d_top_score [R] best proposal score,
+   *n_fallback (host) the number of fallback reads.  Synchronous. */
+MSS_API mss_status mss_map_reads_proposed(mss_ctx* ctx, mss_prop* p, const char* d_reads, const int64_t* d_offsets,
+                                          int32_t R, int32_t max_len, const mss_score_params* sp, int32_t K,
+                                          float tau, mss_hit* d_out, int32_t* d_cand, float* d_top_score,
+                                          int32_t* n_fallback, void* stream);
+/* Checkpoint: master weights and Adam state in a flat file with a header and a CRC-32. */
+MSS_API mss_status mss_prop_save(const mss_prop* p, const char* path);
+MSS_API mss_status mss_prop_load(mss_prop* p, const char* path);
+MSS_API int64_t mss_prop_launch_count(const mss_prop* p);
+
 MSS_API void mss_free(mss_ctx* ctx);
 MSS_API const char* mss_last_error(void);
 

@@ -30,7 +30,11 @@ MSS_HIT_REPEAT = 1
 # every symbol include/maxss.h declares
 EXPORTS = ("mss_load_genome", "mss_load_genome_device", "mss_get_info", "mss_set_frag_len", "mss_set_tune",
            "mss_get_tune", "mss_map_reads", "mss_map_reads_device", "nw_align", "nw_align_device", "nw_align_device_noalloc", "mss_map_align", "mss_sync",
-           "mss_autotune", "mss_scan_timing", "mss_scan_time_ms", "mss_launch_count", "mss_genome_codes", "mss_probe_pipes", "mss_free", "mss_last_error")
+           "mss_autotune", "mss_scan_timing", "mss_scan_time_ms", "mss_launch_count", "mss_genome_codes", "mss_probe_pipes", "mss_prop_create", "mss_prop_free", "mss_prop_param_count",
+           "mss_prop_get_params", "mss_prop_set_params", "mss_prop_read_codes", "mss_prop_window_codes",
+           "mss_prop_embed_device", "mss_prop_grad_device", "mss_prop_train_step", "mss_prop_build_index",
+           "mss_map_reads_proposed", "mss_prop_save", "mss_prop_load", "mss_prop_launch_count", "mss_free",
+           "mss_last_error")
 
 HIT_DTYPE = np.dtype([("best_frag", np.int32), ("second_frag", np.int32), ("best_score", np.int32),
                       ("second_score", np.int32), ("offset", np.int64), ("strand", np.int32), ("flags", np.int32)])
@@ -101,6 +105,23 @@ def load_library(path: str = LIB_PATH):
         "mss_launch_count": ([P], i64),
         "mss_genome_codes": ([P, i64, i64, P], i32),
         "mss_probe_pipes": ([ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], i32),
+        "mss_prop_create": ([ctypes.POINTER(P), ctypes.c_uint64, P], i32),
+        "mss_prop_free": ([P], None),
+        "mss_prop_param_count": ([], i64),
+        "mss_prop_get_params": ([P, P, i64], i32),
+        "mss_prop_set_params": ([P, P, i64], i32),
+        "mss_prop_read_codes": ([P, P, P, P, P, i32, i32, P, P, P], i32),
+        "mss_prop_window_codes": ([P, P, P, i32, i32, i32, P, P, P], i32),
+        "mss_prop_embed_device": ([P, P, P, i32, i32, i32, P, P], i32),
+        "mss_prop_grad_device": ([P, P, P, i32, i32, i32, P, P, P], i32),
+        "mss_prop_train_step": ([P, P, P, i32, i32, i32, P, P, i32, i32, i32, P, ctypes.c_float, ctypes.c_float,
+                                 ctypes.c_float, ctypes.POINTER(ctypes.c_float), P], i32),
+        "mss_prop_build_index": ([P, P, i32, P], i32),
+        "mss_map_reads_proposed": ([P, P, P, P, i32, i32, ctypes.POINTER(ScoreParams), i32, ctypes.c_float, P, P, P,
+                                    ctypes.POINTER(ctypes.c_int32), P], i32),
+        "mss_prop_save": ([P, ctypes.c_char_p], i32),
+        "mss_prop_load": ([P, ctypes.c_char_p], i32),
+        "mss_prop_launch_count": ([P], i64),
         "mss_free": ([P], None),
         "mss_last_error": ([], ctypes.c_char_p),
     }
@@ -316,3 +337,94 @@ def hits_from_bytes(buf) -> np.ndarray:
     """View raw hit bytes (numpy uint8 or a CPU tensor) as HIT_DTYPE records."""
     a = buf.numpy() if hasattr(buf, "numpy") else np.asarray(buf)
     return a.view(HIT_DTYPE)
+
+
+# ---------------------------------------------------------------------------------------------
+# learned fragment proposal
+class Proposal:
+    """The proposal CNN (owns the mss_prop)."""
+
+    def __init__(self, seed: int = 1, stream=None):
+        lib = load_library()
+        h = ctypes.c_void_p()
+        _check(lib.mss_prop_create(ctypes.byref(h), seed, _stream_ptr(stream)), "mss_prop_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    @staticmethod
+    def param_count() -> int:
+        return int(load_library().mss_prop_param_count())
+
+    def get_params(self) -> np.ndarray:
+        n = self.param_count()
+        out = np.zeros(n, dtype=np.float32)
+        _check(_lib.mss_prop_get_params(self._h, _host_ptr(out), n), "mss_prop_get_params")
+        return out
+
+    def set_params(self, w: np.ndarray):
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        _check(_lib.mss_prop_set_params(self._h, _host_ptr(w), w.shape[0]), "mss_prop_set_params")
+
+    def read_codes(self, d_reads, d_offsets, d_idx, d_strand, n, ld, d_codes, d_lens, stream=None):
+        _check(_lib.mss_prop_read_codes(self._h, _host_ptr(d_reads), _host_ptr(d_offsets), _host_ptr(d_idx),
+                                        _host_ptr(d_strand), n, ld, _host_ptr(d_codes), _host_ptr(d_lens),
+                                        _stream_ptr(stream)), "mss_prop_read_codes")
+
+    def window_codes(self, g: Genome, d_starts, n, length, ld, d_codes, d_lens, stream=None):
+        _check(_lib.mss_prop_window_codes(self._h, g.handle, _host_ptr(d_starts), n, length, ld, _host_ptr(d_codes),
+                                          _host_ptr(d_lens), _stream_ptr(stream)), "mss_prop_window_codes")
+
+    def embed(self, d_codes, d_lens, ld, n, maxlen, d_emb, stream=None):
+        _check(_lib.mss_prop_embed_device(self._h, _host_ptr(d_codes), _host_ptr(d_lens), ld, n, maxlen,
+                                          _host_ptr(d_emb), _stream_ptr(stream)), "mss_prop_embed_device")
+
+    def grad(self, d_codes, d_lens, ld, n, maxlen, d_demb, d_grad, stream=None):
+        _check(_lib.mss_prop_grad_device(self._h, _host_ptr(d_codes), _host_ptr(d_lens), ld, n, maxlen,
+                                         _host_ptr(d_demb), _host_ptr(d_grad), _stream_ptr(stream)),
+               "mss_prop_grad_device")
+
+    def train_step(self, d_rcodes, d_rlens, ld_r, B, maxlen_r, d_ccodes, d_clens, ld_c, C, maxlen_c, d_labels,
+                   lr=1e-3, temperature=0.05, weight_decay=0.01, stream=None) -> float:
+        loss = ctypes.c_float()
+        _check(_lib.mss_prop_train_step(self._h, _host_ptr(d_rcodes), _host_ptr(d_rlens), ld_r, B, maxlen_r,
+                                        _host_ptr(d_ccodes), _host_ptr(d_clens), ld_c, C, maxlen_c,
+                                        _host_ptr(d_labels), lr, temperature, weight_decay, ctypes.byref(loss),
+                                        _stream_ptr(stream)), "mss_prop_train_step")
+        return float(loss.value)
+
+    def build_index(self, g: Genome, max_read_len: int, stream=None):
+        _check(_lib.mss_prop_build_index(self._h, g.handle, max_read_len, _stream_ptr(stream)),
+               "mss_prop_build_index")
+
+    def map_reads(self, g: Genome, d_reads, d_offsets, R, max_len, match, mismatch, K, tau, d_out, d_cand=None,
+                  d_top=None, stream=None) -> int:
+        sp = ScoreParams(match, mismatch)
+        nfb = ctypes.c_int32()
+        _check(_lib.mss_map_reads_proposed(g.handle, self._h, _host_ptr(d_reads), _host_ptr(d_offsets), R, max_len,
+                                           ctypes.byref(sp), K, tau, _host_ptr(d_out), _host_ptr(d_cand),
+                                           _host_ptr(d_top), ctypes.byref(nfb), _stream_ptr(stream)),
+               "mss_map_reads_proposed")
+        return int(nfb.value)
+
+    def save(self, path: str):
+        _check(_lib.mss_prop_save(self._h, path.encode()), "mss_prop_save")
+
+    def load(self, path: str):
+        _check(_lib.mss_prop_load(self._h, path.encode()), "mss_prop_load")
+
+    def launch_count(self) -> int:
+        return int(_lib.mss_prop_launch_count(self._h))
+
+    def close(self):
+        if self._h:
+            _lib.mss_prop_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,892 @@
+// Learned fragment proposal (a step added to the method, not in the paper): a small 1-D CNN
+// embeds reads and genome fragments into 128-d unit vectors; the dot product ranks fragments
+// per read so that the exact scan runs only on the top K.
+//
+// Network: one-hot bases (N = all zero) -> 4 x [conv1d k=7 "same", 128 channels, bias, ReLU]
+// -> max over positions -> L2 normalisation.  Weights BF16, accumulation FP32.
+//
+// Kernels (all here, the 128->128 contractions on tensor cores through mma.sync BF16):
+//   k_embed_l1      first layer (4 -> 128) as a gather-sum of per-base weight rows
+//   k_conv_mma      128 -> 128 conv as an implicit GEMM (7 shifted GEMMs, K = 128 per tap);
+//                   forward (bias + ReLU + length mask) and backward-data (flipped, transposed
+//                   weights; the epilogue applies the previous layer's ReLU mask)
+//   k_conv_wgrad    weight gradient, a GEMM over positions per tap (fp32 atomics across CTAs)
+//   k_pool_norm     max over positions (first argmax kept), L2 norm
+//   k_pool_norm_bwd gradient of the norm routed to the argmax positions
+//   k_l1_wgrad      first-layer weight/bias gradients; k_bias_grad: bias gradients
+//   k_ce_loss       softmax cross-entropy of read-vs-candidate logits and its gradients
+//   k_adamw         AdamW on FP32 master weights, refreshing the BF16 copies
+//   k_scores        read x fragment scores (max over the read's two strands)
+//   k_topk          per-read top K (ties -> lower fragment), by 4-round radix select
+//   k_rescore       exact MSS of each read on its K candidate fragments, top-2 among them
+#include <cuda_bf16.h>
+
+#include "../../include/maxss.h"
+#include "common.cuh"
+#include "internal.h"
+#include "prop.h"
+
+namespace mss {
+
+// ------------------------------------------------------------------------------------------
+// shared-memory tiles of 128 bf16 per row, 16-byte chunks XOR-swizzled by the row's low bits
+// so that 8 consecutive rows read by ldmatrix hit 8 different bank groups
+__device__ __forceinline__ uint32_t swz(int row, int chunk) { return (uint32_t)(row * 256 + ((chunk ^ (row & 7)) << 4)); }
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(addr));
+}
+__device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(addr));
+}
+__device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// ------------------------------------------------------------------------------------------
+// layer 1: out[n][p][co] = relu(b[co] + sum_t w1[t][x[p+t-3]][co]) for p < len, else 0
+__global__ void k_embed_l1(const uint8_t* __restrict__ codes, const int32_t* __restrict__ lens, int32_t ld_codes,
+                           const float* __restrict__ w1, const float* __restrict__ b1, __nv_bfloat16* __restrict__ out,
+                           int32_t rows) {
+  const int n = blockIdx.y;
+  const int p = blockIdx.x * 2 + (threadIdx.x >> 7);
+  const int co = threadIdx.x & 127;
+  const int len = lens[n];
+  if (p >= rows - 6) return;
+  float v = 0.f;
+  if (p < len) {
+    v = b1[co];
+#pragma unroll
+    for (int t = 0; t < kPropTaps; ++t) {
+      const int q = p + t - 3;
+      if (q >= 0 && q < len) {
+        const uint32_t c = codes[(int64_t)n * ld_codes + q];
+        if (c < 4) v += w1[(t * 4 + c) * kPropC + co];
+      }
+    }
+    v = fmaxf(v, 0.f);
+  }
+  out[((int64_t)n * rows + p + 3) * kPropC + co] = __float2bfloat16(v);
+}
+
+// ------------------------------------------------------------------------------------------
+// 128 -> 128 conv, one CTA = 128 positions x 128 output channels of one sequence.
+// in/out: [n][rows][128] bf16 (row = position + 3; rows outside [3, len + 3) are zero).
+// w: [7][128 ci][128 co] bf16.  mode 0: out = relu(acc + bias) masked to p < len.
+// mode 1 (backward data): out = acc where prev[n][p + 3][co] > 0 (and p < len), else 0.
+constexpr int kConvM = 128;
+constexpr int kConvThreads = 256;
+constexpr int kConvARows = kConvM + 6;
+constexpr size_t kConvSmem = (size_t)kConvARows * 256 + 2 * 128 * 256;
+
+__global__ void __launch_bounds__(kConvThreads, 2)
+    k_conv_mma(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ w,
+               const float* __restrict__ bias, const __nv_bfloat16* __restrict__ prev, const int32_t* __restrict__ lens,
+               __nv_bfloat16* __restrict__ out, int32_t rows, int mode) {
+  extern __shared__ __align__(128) uint8_t sm[];
+  const uint32_t sA = smem_u32(sm);
+  const uint32_t sW = sA + kConvARows * 256;
+  const int n = blockIdx.y, p0 = blockIdx.x * kConvM;
+  const int len = lens[n];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (p0 >= len) {  // whole tile beyond the sequence: write zeros
+    for (int e = tid; e < kConvM * 16; e += kConvThreads) {
+      const int r = e >> 4, c = e & 15;
+      if (p0 + r < rows - 6)
+        reinterpret_cast<uint4*>(out + ((int64_t)n * rows + p0 + r + 3) * kPropC)[c] = make_uint4(0, 0, 0, 0);
+    }
+    return;
+  }
+  const __nv_bfloat16* inb = in + ((int64_t)n * rows + p0) * kPropC;  // row p0 = position p0 - 3
+  for (int e = tid; e < kConvARows * 16; e += kConvThreads) {
+    const int r = e >> 4, c = e & 15;
+    cp_async16(sA + swz(r, c), inb + r * kPropC + c * 8);
+  }
+  auto load_w = [&](int t, int buf) {
+    const __nv_bfloat16* wt = w + (int64_t)t * kPropC * kPropC;
+    const uint32_t base = sW + buf * 128 * 256;
+    for (int e = tid; e < 128 * 16; e += kConvThreads) {
+      const int r = e >> 4, c = e & 15;
+      cp_async16(base + swz(r, c), wt + r * kPropC + c * 8);
+    }
+  };
+  load_w(0, 0);
+  cp_async_commit();
+
+  const int wm = warp & 3, wn = warp >> 2;  // warp tile: positions wm*32 + [0,32), channels wn*64 + [0,64)
+  float acc[2][8][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+
+  for (int t = 0; t < kPropTaps; ++t) {
+    if (t + 1 < kPropTaps) {
+      load_w(t + 1, (t + 1) & 1);
+      cp_async_commit();
+      cp_async_wait_1();
+    } else {
+      cp_async_wait_all();
+    }
+    __syncthreads();
+    const uint32_t wbase = sW + (t & 1) * 128 * 256;
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk) {  // 16 input channels per step
+      uint32_t af[2][4];
+#pragma unroll
+      for (int mi = 0; mi < 2; ++mi) {
+        const int i = lane >> 3;
+        const int r = wm * 32 + mi * 16 + (i & 1) * 8 + (lane & 7) + t;  // tap t shifts the rows
+        const int ch = kk * 2 + (i >> 1);
+        ldsm_x4(sA + swz(r, ch), af[mi][0], af[mi][1], af[mi][2], af[mi][3]);
+      }
+#pragma unroll
+      for (int nj = 0; nj < 8; nj += 2) {
+        const int i = lane >> 3;
+        const int r = kk * 16 + (i & 1) * 8 + (lane & 7);
+        const int ch = (wn * 64 + nj * 8) / 8 + (i >> 1);
+        uint32_t b0, b1, b2, b3;
+        ldsm_x4_t(wbase + swz(r, ch), b0, b1, b2, b3);
+#pragma unroll
+        for (int mi = 0; mi < 2; ++mi) {
+          mma_bf16(acc[mi][nj], af[mi], b0, b1);
+          mma_bf16(acc[mi][nj + 1], af[mi], b2, b3);
+        }
+      }
+    }
+    __syncthreads();  // the weight buffer of tap t is rewritten at t + 2
+  }
+  // epilogue
+#pragma unroll
+  for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+    for (int nj = 0; nj < 8; ++nj)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int p = p0 + wm * 32 + mi * 16 + (lane >> 2) + h * 8;
+        const int co = wn * 64 + nj * 8 + (lane & 3) * 2;
+        if (p >= rows - 6) continue;
+        float v0 = acc[mi][nj][h * 2], v1 = acc[mi][nj][h * 2 + 1];
+        const int64_t o = ((int64_t)n * rows + p + 3) * kPropC + co;
+        if (p >= len) {
+          v0 = v1 = 0.f;
+        } else if (mode == 0) {
+          v0 = fmaxf(v0 + bias[co], 0.f);
+          v1 = fmaxf(v1 + bias[co + 1], 0.f);
+        } else {
+          const __nv_bfloat162 pv = *reinterpret_cast<const __nv_bfloat162*>(prev + o);
+          if (__bfloat162float(pv.x) <= 0.f) v0 = 0.f;
+          if (__bfloat162float(pv.y) <= 0.f) v1 = 0.f;
+        }
+        *reinterpret_cast<__nv_bfloat162*>(out + o) = __floats2bfloat162_rn(v0, v1);
+      }
+}
+
+// ------------------------------------------------------------------------------------------
+// weight gradient of a 128 -> 128 layer for one tap t: dw[t][ci][co] += sum_{n, p} in[n][p + t - 3][ci]
+// * g[n][p][co].  The (sequence, 128-position tile) pairs are split into contiguous runs, one
+// run per CTA; a CTA accumulates its run in registers and adds it to dw once (fp32 atomics).
+__global__ void __launch_bounds__(kConvThreads, 2)
+    k_conv_wgrad(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ g,
+                 const int32_t* __restrict__ lens, float* __restrict__ dw, int32_t n_seq, int32_t rows,
+                 int32_t tiles_per_cta) {
+  extern __shared__ __align__(128) uint8_t sm[];
+  const uint32_t sA = smem_u32(sm);          // in rows (positions p0 - 3 ...), 134 rows
+  const uint32_t sB = sA + kConvARows * 256;  // g rows of positions p0 .. p0 + 127
+  const int t = blockIdx.y;
+  const int tiles_per_seq = (rows - 6) / kConvM;
+  const int64_t total = (int64_t)n_seq * tiles_per_seq;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int wm = warp & 3, wn = warp >> 2;  // warp tile: ci wm*32 + [0,32), co wn*64 + [0,64)
+  float acc[2][8][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+  bool any = false;
+  for (int64_t tile = (int64_t)blockIdx.x * tiles_per_cta;
+       tile < total && tile < (int64_t)(blockIdx.x + 1) * tiles_per_cta; ++tile) {
+    const int n = (int)(tile / tiles_per_seq);
+    const int p0 = (int)(tile - (int64_t)n * tiles_per_seq) * kConvM;
+    if (p0 >= lens[n]) continue;  // uniform across the CTA
+    any = true;
+    __syncthreads();  // the previous tile's shared data is no longer read
+    const __nv_bfloat16* inb = in + ((int64_t)n * rows + p0) * kPropC;
+    for (int e = tid; e < kConvARows * 16; e += kConvThreads) {
+      const int r = e >> 4, c = e & 15;
+      cp_async16(sA + swz(r, c), inb + r * kPropC + c * 8);
+    }
+    const __nv_bfloat16* gb = g + ((int64_t)n * rows + p0 + 3) * kPropC;
+    for (int e = tid; e < 128 * 16; e += kConvThreads) {
+      const int r = e >> 4, c = e & 15;
+      cp_async16(sB + swz(r, c), gb + r * kPropC + c * 8);
+    }
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+#pragma unroll 2
+    for (int kk = 0; kk < 8; ++kk) {  // 16 positions per step
+      uint32_t af[2][4];
+#pragma unroll
+      for (int mi = 0; mi < 2; ++mi) {
+        // A[m = ci][k = p] = in[p + t - 3][ci]: transposed load of the [p][ci] tile
+        const int i = lane >> 3;
+        const int r = kk * 16 + (i >> 1) * 8 + (lane & 7) + t;
+        const int ch = (wm * 32 + mi * 16) / 8 + (i & 1);
+        ldsm_x4_t(sA + swz(r, ch), af[mi][0], af[mi][1], af[mi][2], af[mi][3]);
+      }
+#pragma unroll
+      for (int nj = 0; nj < 8; nj += 2) {
+        const int i = lane >> 3;
+        const int r = kk * 16 + (i & 1) * 8 + (lane & 7);
+        const int ch = (wn * 64 + nj * 8) / 8 + (i >> 1);
+        uint32_t b0, b1, b2, b3;
+        ldsm_x4_t(sB + swz(r, ch), b0, b1, b2, b3);
+#pragma unroll
+        for (int mi = 0; mi < 2; ++mi) {
+          mma_bf16(acc[mi][nj], af[mi], b0, b1);
+          mma_bf16(acc[mi][nj + 1], af[mi], b2, b3);
+        }
+      }
+    }
+  }
+  if (!any) return;
+  float* dwt = dw + (int64_t)t * kPropC * kPropC;
+#pragma unroll
+  for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+    for (int nj = 0; nj < 8; ++nj)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int ci = wm * 32 + mi * 16 + (lane >> 2) + h * 8;
+        const int co = wn * 64 + nj * 8 + (lane & 3) * 2;
+        atomicAdd(dwt + ci * kPropC + co, acc[mi][nj][h * 2]);
+        atomicAdd(dwt + ci * kPropC + co + 1, acc[mi][nj][h * 2 + 1]);
+      }
+}
+
+// bias gradient: db[co] += sum_{n, p < len} g[n][p + 3][co]
+__global__ void k_bias_grad(const __nv_bfloat16* __restrict__ g, const int32_t* __restrict__ lens, float* db,
+                            int32_t rows) {
+  const int n = blockIdx.y, co = threadIdx.x & 127, half = threadIdx.x >> 7;
+  const int len = lens[n];
+  float s = 0.f;
+  for (int p = blockIdx.x * 2 + half; p < len; p += gridDim.x * 2)
+    s += __bfloat162float(g[((int64_t)n * rows + p + 3) * kPropC + co]);
+  atomicAdd(db + co, s);
+}
+
+// first layer gradients: dw1[t][c][co] += g[p][co] for x[p + t - 3] == c; db1[co] += g[p][co]
+__global__ void k_l1_wgrad(const uint8_t* __restrict__ codes, const int32_t* __restrict__ lens, int32_t ld_codes,
+                           const __nv_bfloat16* __restrict__ g, float* dw1, float* db1, int32_t rows) {
+  __shared__ float s_w[kPropTaps * 4][kPropC];
+  __shared__ float s_b[kPropC];
+  const int n = blockIdx.y, co = threadIdx.x;
+  for (int e = threadIdx.x; e < kPropTaps * 4 * kPropC; e += blockDim.x) (&s_w[0][0])[e] = 0.f;
+  if (co < kPropC) s_b[co] = 0.f;
+  __syncthreads();
+  const int len = lens[n];
+  for (int p = blockIdx.x; p < len; p += gridDim.x) {
+    const float gv = __bfloat162float(g[((int64_t)n * rows + p + 3) * kPropC + co]);
+    if (gv == 0.f) continue;
+    s_b[co] += gv;
+#pragma unroll
+    for (int t = 0; t < kPropTaps; ++t) {
+      const int q = p + t - 3;
+      if (q >= 0 && q < len) {
+        const uint32_t c = codes[(int64_t)n * ld_codes + q];
+        if (c < 4) s_w[t * 4 + c][co] += gv;
+      }
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < kPropTaps * 4 * kPropC; e += blockDim.x) {
+    const float v = (&s_w[0][0])[e];
+    if (v != 0.f) atomicAdd(dw1 + e, v);
+  }
+  if (s_b[co] != 0.f) atomicAdd(db1 + co, s_b[co]);
+}
+
+// ------------------------------------------------------------------------------------------
+// max over positions p < len (first maximum), L2 norm.  One CTA (128 threads) per sequence.
+__global__ void k_pool_norm(const __nv_bfloat16* __restrict__ act, const int32_t* __restrict__ lens, int32_t rows,
+                            float* __restrict__ emb, float* __restrict__ norms, int32_t* __restrict__ argmax) {
+  const int n = blockIdx.x, co = threadIdx.x;
+  const int len = lens[n];
+  float best = -1.f;
+  int bi = 0;
+  for (int p = 0; p < len; ++p) {
+    const float v = __bfloat162float(act[((int64_t)n * rows + p + 3) * kPropC + co]);
+    if (v > best) {
+      best = v;
+      bi = p;
+    }
+  }
+  if (len <= 0) best = 0.f;
+  __shared__ float red[4];
+  float sq = best * best;
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, s);
+  if ((co & 31) == 0) red[co >> 5] = sq;
+  __syncthreads();
+  const float nrm = sqrtf(red[0] + red[1] + red[2] + red[3]) + 1e-6f;
+  emb[n * kPropC + co] = best / nrm;
+  if (argmax) argmax[n * kPropC + co] = bi;
+  if (norms && co == 0) norms[n] = nrm;
+}
+
+// gradient through the L2 norm and the max pool: g4[n][argmax + 3][co] = de_raw if act > 0
+__global__ void k_pool_norm_bwd(const float* __restrict__ emb, const float* __restrict__ demb,
+                                const float* __restrict__ norms, const int32_t* __restrict__ argmax,
+                                const __nv_bfloat16* __restrict__ act, const int32_t* __restrict__ lens, int32_t rows,
+                                __nv_bfloat16* __restrict__ g4) {
+  const int n = blockIdx.x, co = threadIdx.x;
+  __shared__ float red[4];
+  const float e = emb[n * kPropC + co], de = demb[n * kPropC + co];
+  float dot = e * de;
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, s);
+  if ((co & 31) == 0) red[co >> 5] = dot;
+  __syncthreads();
+  dot = red[0] + red[1] + red[2] + red[3];
+  const float draw = (de - e * dot) / norms[n];
+  if (lens[n] <= 0) return;
+  const int p = argmax[n * kPropC + co];
+  const int64_t o = ((int64_t)n * rows + p + 3) * kPropC + co;
+  if (__bfloat162float(act[o]) > 0.f) g4[o] = __float2bfloat16(draw);
+}
+
+// ------------------------------------------------------------------------------------------
+// softmax cross-entropy: logits[i][j] = <r_i, c_j> / temp over the C candidates, label[i];
+// loss[i], dr[i] = sum_j (p_ij - y_ij) c_j / temp, dc[j] += (p_ij - y_ij) r_i / temp.
+// One CTA (128 threads) per read; C <= 1024.
+__global__ void k_ce_loss(const float* __restrict__ r, const float* __restrict__ c, const int32_t* __restrict__ label,
+                          int32_t C, float inv_temp, float* __restrict__ loss, float* __restrict__ dr,
+                          float* __restrict__ dc, float scale) {
+  __shared__ float s_r[kPropC];
+  __shared__ float s_p[1024];
+  __shared__ float red[4];
+  const int i = blockIdx.x, tid = threadIdx.x;
+  s_r[tid] = r[i * kPropC + tid];
+  __syncthreads();
+  for (int j = tid; j < C; j += blockDim.x) {
+    float s = 0.f;
+    for (int k = 0; k < kPropC; ++k) s += s_r[k] * c[j * kPropC + k];
+    s_p[j] = s * inv_temp;
+  }
+  __syncthreads();
+  float mx = -1e30f;
+  for (int j = tid; j < C; j += blockDim.x) mx = fmaxf(mx, s_p[j]);
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, s));
+  if ((tid & 31) == 0) red[tid >> 5] = mx;
+  __syncthreads();
+  mx = fmaxf(fmaxf(red[0], red[1]), fmaxf(red[2], red[3]));
+  __syncthreads();
+  float se = 0.f;
+  for (int j = tid; j < C; j += blockDim.x) {
+    const float ex = __expf(s_p[j] - mx);
+    s_p[j] = ex;
+    se += ex;
+  }
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1) se += __shfl_xor_sync(0xffffffffu, se, s);
+  if ((tid & 31) == 0) red[tid >> 5] = se;
+  __syncthreads();
+  se = red[0] + red[1] + red[2] + red[3];
+  const int lab = label[i];
+  const bool lab_ok = lab >= 0 && lab < C;  // an out-of-range label yields NaN loss, no gradient term
+  for (int j = tid; j < C; j += blockDim.x) s_p[j] = s_p[j] / se - (j == lab ? 1.f : 0.f);
+  __syncthreads();
+  if (tid == 0) loss[i] = lab_ok ? -logf(fmaxf((s_p[lab] + 1.f), 1e-30f)) : __int_as_float(0x7fc00000);
+  // dr
+  float acc = 0.f;
+  for (int j = 0; j < C; ++j) acc += s_p[j] * c[j * kPropC + tid];
+  dr[i * kPropC + tid] = acc * inv_temp * scale;
+  for (int j = 0; j < C; ++j) atomicAdd(dc + j * kPropC + tid, s_p[j] * s_r[tid] * inv_temp * scale);
+}
+
+// AdamW step on fp32 master weights; refreshes the bf16 copy when given
+__global__ void k_adamw(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m1,
+                        float* __restrict__ m2, __nv_bfloat16* __restrict__ wb, int64_t count, float lr, float beta1,
+                        float beta2, float eps, float wd, float bc1, float bc2) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const float gi = g[i];
+  const float a = beta1 * m1[i] + (1.f - beta1) * gi;
+  const float b = beta2 * m2[i] + (1.f - beta2) * gi * gi;
+  m1[i] = a;
+  m2[i] = b;
+  float wi = w[i] * (1.f - lr * wd);
+  wi -= lr * (a / bc1) / (sqrtf(b / bc2) + eps);
+  w[i] = wi;
+  if (wb) wb[i] = __float2bfloat16(wi);
+}
+
+// flipped, transposed copy for the backward-data pass: wt[t][co][ci] = w[6 - t][ci][co]
+__global__ void k_flip_weights(const __nv_bfloat16* __restrict__ w, __nv_bfloat16* __restrict__ wt) {
+  const int t = blockIdx.x, ci = threadIdx.x;
+  for (int co = 0; co < kPropC; ++co)
+    wt[((int64_t)t * kPropC + co) * kPropC + ci] = w[((int64_t)(kPropTaps - 1 - t) * kPropC + ci) * kPropC + co];
+}
+
+// ------------------------------------------------------------------------------------------
+// scores[i][f] = max(<e_fwd_i, e_f>, <e_rev_i, e_f>); a CTA takes 8 reads x 128 fragments
+__global__ void k_scores(const float* __restrict__ er, int32_t R, const __nv_bfloat16* __restrict__ ef, int64_t NF,
+                         float* __restrict__ scores) {
+  __shared__ float s_e[16][kPropC];
+  const int r0 = blockIdx.y * 8;
+  for (int e = threadIdx.x; e < 16 * kPropC; e += blockDim.x) {
+    const int q = e / kPropC, k = e % kPropC;
+    const int read = r0 + (q >> 1);
+    s_e[q][k] = read < R ? er[((int64_t)read * 2 + (q & 1)) * kPropC + k] : 0.f;
+  }
+  __syncthreads();
+  const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= NF) return;
+  float acc[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) acc[q] = 0.f;
+  const __nv_bfloat162* fr = reinterpret_cast<const __nv_bfloat162*>(ef + f * kPropC);
+  for (int k2 = 0; k2 < kPropC / 2; ++k2) {
+    const float2 v = __bfloat1622float2(fr[k2]);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc[q] += s_e[q][2 * k2] * v.x + s_e[q][2 * k2 + 1] * v.y;
+  }
+#pragma unroll
+  for (int q = 0; q < 16; q += 2) {
+    const int read = r0 + (q >> 1);
+    if (read < R) scores[(int64_t)read * NF + f] = fmaxf(acc[q], acc[q + 1]);
+  }
+}
+
+// order-preserving key of a float
+__device__ __forceinline__ uint32_t fkey(float x) {
+  const uint32_t u = __float_as_uint(x);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+// per-read top K of scores[i][0..NF) (largest first; ties -> lower fragment); one CTA per read:
+// 4-round radix select of the K-th largest key, then the elements above it plus the lowest-
+// indexed elements equal to it, sorted.
+__global__ void k_topk(const float* __restrict__ scores, int64_t NF, int32_t K, int32_t* __restrict__ out_f,
+                       float* __restrict__ out_s) {
+  __shared__ uint32_t hist[256];
+  __shared__ uint32_t s_prefix, s_mask, s_need;
+  __shared__ int32_t s_cnt_gt, s_cnt_eq;
+  __shared__ uint32_t s_key[1024];
+  __shared__ int32_t s_idx[1024];
+  const int i = blockIdx.x, tid = threadIdx.x;
+  const float* sc = scores + (int64_t)i * NF;
+  const int32_t Kc = (int32_t)(NF < (int64_t)K ? NF : K);
+  if (tid == 0) {
+    s_prefix = 0;
+    s_mask = 0;
+    s_need = (uint32_t)Kc;
+  }
+  __syncthreads();
+  for (int round = 0; round < 4; ++round) {
+    const int shift = 24 - 8 * round;
+    for (int b = tid; b < 256; b += blockDim.x) hist[b] = 0;
+    __syncthreads();
+    const uint32_t pre = s_prefix, msk = s_mask;
+    for (int64_t f = tid; f < NF; f += blockDim.x) {
+      const uint32_t k = fkey(sc[f]);
+      if ((k & msk) == pre) atomicAdd(&hist[(k >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    if (tid == 0) {  // walk buckets from the top until the K-th element is reached
+      uint32_t need = s_need, b = 255;
+      for (;; --b) {
+        if (hist[b] >= need || b == 0) break;
+        need -= hist[b];
+      }
+      s_prefix = pre | (b << shift);
+      s_mask = msk | (255u << shift);
+      s_need = need;
+    }
+    __syncthreads();
+  }
+  const uint32_t kth = s_prefix;  // key of the K-th largest element
+  if (tid == 0) {
+    s_cnt_gt = 0;
+    s_cnt_eq = 0;
+  }
+  __syncthreads();
+  // elements strictly above the K-th key (fewer than K), then ties in fragment order
+  for (int64_t f = tid; f < NF; f += blockDim.x) {
+    const uint32_t k = fkey(sc[f]);
+    if (k > kth) {
+      const int slot = atomicAdd(&s_cnt_gt, 1);
+      if (slot < 1024) {
+        s_key[slot] = k;
+        s_idx[slot] = (int32_t)f;
+      }
+    }
+  }
+  __syncthreads();
+  const int ngt = s_cnt_gt;
+  const int need_eq = Kc - ngt;
+  // lowest-indexed ties: collect the equal keys in parallel (usually a handful), keep the
+  // need_eq smallest indices; with very many ties fall back to an ordered scan
+  __shared__ int32_t s_tie[1024];
+  __shared__ int32_t s_ntie;
+  if (tid == 0) s_ntie = 0;
+  __syncthreads();
+  for (int64_t f = tid; f < NF; f += blockDim.x)
+    if (fkey(sc[f]) == kth) {
+      const int slot = atomicAdd(&s_ntie, 1);
+      if (slot < 1024) s_tie[slot] = (int32_t)f;
+    }
+  __syncthreads();
+  const int ntie = s_ntie;
+  if (ntie <= 1024) {
+    for (int a = tid; a < ntie; a += blockDim.x) {
+      int rank = 0;
+      for (int b = 0; b < ntie; ++b) rank += s_tie[b] < s_tie[a];
+      if (rank < need_eq) {
+        s_key[ngt + rank] = kth;
+        s_idx[ngt + rank] = s_tie[a];
+      }
+    }
+    if (tid == 0) s_cnt_eq = ntie < need_eq ? ntie : need_eq;
+  } else if (tid == 0) {
+    int taken = 0;
+    for (int64_t f = 0; f < NF && taken < need_eq; ++f)
+      if (fkey(sc[f]) == kth) {
+        s_key[ngt + taken] = kth;
+        s_idx[ngt + taken] = (int32_t)f;
+        ++taken;
+      }
+    s_cnt_eq = taken;
+  }
+  __syncthreads();
+  const int tot = ngt + s_cnt_eq;
+  // sort (key desc, index asc) by rank counting (tot <= K <= 1024)
+  for (int a = tid; a < tot; a += blockDim.x) {
+    int rank = 0;
+    for (int b = 0; b < tot; ++b)
+      rank += (s_key[b] > s_key[a]) || (s_key[b] == s_key[a] && s_idx[b] < s_idx[a]);
+    out_f[(int64_t)i * K + rank] = s_idx[a];
+    if (out_s) out_s[(int64_t)i * K + rank] = sc[s_idx[a]];
+  }
+  for (int a = tot + tid; a < K; a += blockDim.x) {
+    out_f[(int64_t)i * K + a] = -1;
+    if (out_s) out_s[(int64_t)i * K + a] = -1e30f;
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// exact rescoring: one warp per read; for each of its K candidate fragments the MSS of every
+// diagonal on both strands (int32, the plain recurrence), the fragment maximum, and the top-2
+// among the candidates (ties -> lower fragment) with the best diagonal (ties: + strand, then
+// smaller d).  Writes an mss_hit per read (second fragment / score among the candidates).
+constexpr int kRsWarps = 4;
+constexpr int kRsChunk = 512;
+
+__global__ void __launch_bounds__(kRsWarps * 32)
+    k_rescore(const uint32_t* __restrict__ g2, const uint32_t* __restrict__ gm, int64_t F, const char* __restrict__ reads,
+              const int64_t* __restrict__ offsets, const int32_t* __restrict__ idx, int32_t R,
+              const int32_t* __restrict__ cand, int32_t K, int32_t match, int32_t mismatch, void* hits,
+              int32_t* __restrict__ cand_scores) {
+  __shared__ uint8_t s_gen[kRsWarps][kRsChunk + MSS_MAX_READ_LEN + 16];
+  __shared__ uint8_t s_q[kRsWarps][2][MSS_MAX_READ_LEN];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int i = blockIdx.x * kRsWarps + wib;
+  if (i >= R) return;
+  const int ridx = idx ? idx[i] : i;
+  const int64_t off = offsets[ridx];
+  int64_t l = offsets[ridx + 1] - off;
+  const int32_t m = l < 0 ? 0 : (l > MSS_MAX_READ_LEN ? MSS_MAX_READ_LEN : (int32_t)l);
+  for (int k = lane; k < m; k += 32) {
+    uint32_t cf = ascii_code((uint8_t)reads[off + k]);
+    if (cf > 4) cf = 4;
+    s_q[wib][0][k] = (uint8_t)cf;
+    s_q[wib][1][m - 1 - k] = (uint8_t)(cf < 4 ? 3 - cf : 4);
+  }
+  __syncwarp();
+  int32_t s1 = -1, f1 = 0x7fffffff, s2 = -1, f2 = 0x7fffffff, bS = 0;
+  int64_t bD = 0;
+  for (int c = 0; c < K; ++c) {
+    const int32_t f = cand[(int64_t)i * K + c];
+    if (f < 0) continue;
+    int32_t bestK = -1, bestS = 0;
+    int64_t bestD = 0;
+    const int64_t d_lo = (int64_t)f * F, d_hi = d_lo + F;
+    for (int sg = 0; sg < 2; ++sg) {
+      for (int64_t d0 = d_lo; d0 < d_hi; d0 += kRsChunk) {
+        const int64_t nd = (d_hi - d0 < (int64_t)kRsChunk) ? d_hi - d0 : (int64_t)kRsChunk;
+        __syncwarp();
+        for (int64_t x = lane; x < nd + m; x += 32) s_gen[wib][x] = (uint8_t)genome_code(g2, gm, d0 + x);
+        __syncwarp();
+        for (int64_t x = lane; x < nd; x += 32) {
+          int32_t h = 0, mx = 0;
+          for (int k = 0; k < m; ++k) {
+            const uint32_t qc = s_q[wib][sg][k], gc = s_gen[wib][x + k];
+            h += (qc < 4 && qc == gc) ? match : mismatch;
+            h = max(h, 0);
+            mx = max(mx, h);
+          }
+          if (mx > bestK) {
+            bestK = mx;
+            bestS = sg;
+            bestD = d0 + x;
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) {
+      const int32_t oK = __shfl_xor_sync(0xffffffffu, bestK, s);
+      const int32_t oS = __shfl_xor_sync(0xffffffffu, bestS, s);
+      const int64_t oD = __shfl_xor_sync(0xffffffffu, bestD, s);
+      if (oK > bestK || (oK == bestK && (oS < bestS || (oS == bestS && oD < bestD)))) {
+        bestK = oK;
+        bestS = oS;
+        bestD = oD;
+      }
+    }
+    if (cand_scores && lane == 0) cand_scores[(int64_t)i * K + c] = bestK;
+    // top-2 over candidates (distinct fragments; the list may repeat none)
+    if (bestK > s1 || (bestK == s1 && f < f1)) {
+      s2 = s1;
+      f2 = f1;
+      s1 = bestK;
+      f1 = f;
+      bS = bestS;
+      bD = bestD;
+    } else if (f != f1 && (bestK > s2 || (bestK == s2 && f < f2))) {
+      s2 = bestK;
+      f2 = f;
+    }
+  }
+  if (lane == 0) {
+    mss_hit h;
+    h.best_frag = s1 < 0 ? -1 : f1;
+    h.best_score = s1 < 0 ? 0 : s1;
+    h.second_frag = s2 < 0 ? -1 : f2;
+    h.second_score = s2 < 0 ? 0 : s2;
+    h.offset = bD;
+    h.strand = bS;
+    const bool repeat = (h.best_score == 0) || (10LL * h.second_score >= 9LL * h.best_score);
+    h.flags = repeat ? MSS_HIT_REPEAT : 0;
+    reinterpret_cast<mss_hit*>(hits)[i] = h;
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// host launchers
+cudaError_t prop_embed_l1(const uint8_t* codes, const int32_t* lens, int32_t ld, int32_t n, const float* w1,
+                          const float* b1, __nv_bfloat16* out, int32_t rows, cudaStream_t s) {
+  dim3 grid((unsigned)((rows - 6 + 1) / 2), (unsigned)n);
+  k_embed_l1<<<grid, 256, 0, s>>>(codes, lens, ld, w1, b1, out, rows);
+  return cudaGetLastError();
+}
+
+cudaError_t prop_conv(const __nv_bfloat16* in, const __nv_bfloat16* w, const float* bias, const __nv_bfloat16* prev,
+                      const int32_t* lens, __nv_bfloat16* out, int32_t n, int32_t rows, int mode, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_conv_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kConvSmem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_conv_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kConvSmem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  dim3 grid((unsigned)((rows - 6) / kConvM), (unsigned)n);
+  k_conv_mma<<<grid, kConvThreads, kConvSmem, s>>>(in, w, bias, prev, lens, out, rows, mode);
+  return cudaGetLastError();
+}
+
+cudaError_t prop_conv_wgrad(const __nv_bfloat16* in, const __nv_bfloat16* g, const int32_t* lens, float* dw, int32_t n,
+                            int32_t rows, cudaStream_t s) {
+  const int64_t total = (int64_t)n * ((rows - 6) / kConvM);
+  const int64_t ctas = total < 64 ? total : 64;  // runs of tiles per tap
+  const int32_t per = (int32_t)((total + ctas - 1) / ctas);
+  dim3 grid((unsigned)((total + per - 1) / per), (unsigned)kPropTaps);
+  k_conv_wgrad<<<grid, kConvThreads, kConvSmem, s>>>(in, g, lens, dw, n, rows, per);
+  return cudaGetLastError();
+}
+
+cudaError_t prop_bias_grad(const __nv_bfloat16* g, const int32_t* lens, float* db, int32_t n, int32_t rows,
+                           cudaStream_t s) {
+  dim3 grid(16, (unsigned)n);
+  k_bias_grad<<<grid, 256, 0, s>>>(g, lens, db, rows);
+  return cudaGetLastError();
+}
+
+cudaError_t prop_l1_wgrad(const uint8_t* codes, const int32_t* lens, int32_t ld, const __nv_bfloat16* g, float* dw1,
+                          float* db1, int32_t n, int32_t rows, cudaStream_t s) {
+  dim3 grid(2, (unsigned)n);
+  k_l1_wgrad<<<grid, kPropC, 0, s>>>(codes, lens, ld, g, dw1, db1, rows);
+  return cudaGetLastError();
+}
+
+cudaError_t prop_pool_norm(const __nv_bfloat16* act, const int32_t* lens, int32_t n, int32_t rows, float* emb,
+                           float* norms, int32_t* argmax, cudaStream_t s) {
+  k_pool_norm<<<n, kPropC, 0, s>>>(act, lens, rows, emb, norms, argmax);
+  return cudaGetLastError();
+}
+
+cudaError_t prop_pool_norm_bwd(const float* emb, const float* demb, const float* norms, const int32_t* argmax,
+                               const __nv_bfloat16* act, const int32_t* lens, int32_t n, int32_t rows,
+                               __nv_bfloat16* g4, cudaStream_t s) {
+  k_pool_norm_bwd<<<n, kPropC, 0, s>>>(emb, demb, norms, argmax, act, lens, rows, g4);
+  return cudaGetLastError();
+}
+
+cudaError_t prop_ce_loss(const float* r, const float* c, const int32_t* label, int32_t B, int32_t C, float inv_temp,
+                         float* loss, float* dr, float* dc, float scale, cudaStream_t s) {
+  if (C > 1024) return cudaErrorInvalidValue;
+  k_ce_loss<<<B, kPropC, 0, s>>>(r, c, label, C, inv_temp, loss, dr, dc, scale);
+  return cudaGetLastError();
+}
+
+cudaError_t prop_adamw(float* w, const float* g, float* m1, float* m2, __nv_bfloat16* wb, int64_t count, float lr,
+                       float beta1, float beta2, float eps, float wd, float bc1, float bc2, cudaStream_t s) {
+  k_adamw<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(w, g, m1, m2, wb, count, lr, beta1, beta2, eps, wd, bc1,
+                                                          bc2);
+  return cudaGetLastError();
+}
+
+cudaError_t prop_flip_weights(const __nv_bfloat16* w, __nv_bfloat16* wt, cudaStream_t s) {
+  k_flip_weights<<<kPropTaps, kPropC, 0, s>>>(w, wt);
+  return cudaGetLastError();
+}
+
+cudaError_t prop_scores(const float* er, int32_t R, const __nv_bfloat16* ef, int64_t NF, float* scores,
+                        cudaStream_t s) {
+  dim3 grid((unsigned)((NF + 127) / 128), (unsigned)((R + 7) / 8));
+  k_scores<<<grid, 128, 0, s>>>(er, R, ef, NF, scores);
+  return cudaGetLastError();
+}
+
+cudaError_t prop_topk(const float* scores, int32_t R, int64_t NF, int32_t K, int32_t* out_f, float* out_s,
+                      cudaStream_t s) {
+  if (K > 1024) return cudaErrorInvalidValue;
+  k_topk<<<R, 256, 0, s>>>(scores, NF, K, out_f, out_s);
+  return cudaGetLastError();
+}
+
+cudaError_t prop_rescore(const uint32_t* g2, const uint32_t* gm, int64_t F, const char* reads, const int64_t* offsets,
+                         const int32_t* idx, int32_t R, const int32_t* cand, int32_t K, int32_t match,
+                         int32_t mismatch, void* hits, int32_t* cand_scores, cudaStream_t s) {
+  if (R <= 0) return cudaSuccess;
+  k_rescore<<<(R + kRsWarps - 1) / kRsWarps, kRsWarps * 32, 0, s>>>(g2, gm, F, reads, offsets, idx, R, cand, K, match,
+                                                                     mismatch, hits, cand_scores);
+  return cudaGetLastError();
+}
+
+}  // namespace mss
+
+namespace mss {
+
+// ------------------------------------------------------------------------------------------
+// input codes: reads (forward or reverse complement) and genome windows (N beyond the genome)
+__global__ void k_read_codes(const char* __restrict__ reads, const int64_t* __restrict__ offsets,
+                             const int32_t* __restrict__ idx, const int8_t* __restrict__ strand, int32_t n, int32_t ld,
+                             uint8_t* __restrict__ codes, int32_t* __restrict__ lens) {
+  const int i = blockIdx.x;
+  if (i >= n) return;
+  const int r = idx ? idx[i] : i;
+  const int64_t off = offsets[r];
+  int64_t l = offsets[r + 1] - off;
+  const int32_t m = (int32_t)(l < 0 ? 0 : (l > ld ? ld : l));
+  const bool rc = strand && strand[i];
+  for (int k = threadIdx.x; k < ld; k += blockDim.x) {
+    uint32_t c = 4;
+    if (k < m) {
+      c = ascii_code((uint8_t)reads[off + (rc ? (m - 1 - k) : k)]);
+      if (c > 4) c = 4;
+      if (rc && c < 4) c = 3 - c;
+    }
+    codes[(int64_t)i * ld + k] = (uint8_t)c;
+  }
+  if (threadIdx.x == 0) lens[i] = m;
+}
+
+__global__ void k_window_codes(const uint32_t* __restrict__ g2, const uint32_t* __restrict__ gm,
+                               const int64_t* __restrict__ starts, int32_t n, int32_t len, int32_t ld,
+                               uint8_t* __restrict__ codes, int32_t* __restrict__ lens) {
+  const int i = blockIdx.x;
+  if (i >= n) return;
+  const int64_t s = starts[i];
+  for (int k = threadIdx.x; k < ld; k += blockDim.x)
+    codes[(int64_t)i * ld + k] = (uint8_t)(k < len ? genome_code(g2, gm, s + k) : 4u);
+  if (threadIdx.x == 0) lens[i] = len;
+}
+
+// deterministic initialisation: uniform(-a, a) with a = sqrt(6 / fan_in), biases 0.01; the
+// uniform draw is a SplitMix64-style hash of (seed, index)
+__device__ __forceinline__ float hash_uniform(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + 0x9E3779B97F4A7C15ull * (i + 1);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (float)((z >> 40) * (1.0 / 16777216.0)) * 2.f - 1.f;
+}
+
+__global__ void k_init_params(float* w, uint64_t seed) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= kPropParams) return;
+  float v;
+  if (i < kPropW1) {
+    v = hash_uniform(seed, i) * sqrtf(6.f / (4 * kPropTaps));
+  } else if (i < kPropW1 + kPropC) {
+    v = 0.01f;
+  } else {
+    const int64_t j = (i - kPropW1 - kPropC) % (kPropWl + kPropC);
+    v = j < kPropWl ? hash_uniform(seed, i) * sqrtf(6.f / (kPropC * kPropTaps)) : 0.01f;
+  }
+  w[i] = v;
+}
+
+__global__ void k_to_bf16(const float* __restrict__ w, __nv_bfloat16* __restrict__ wb, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) wb[i] = __float2bfloat16(w[i]);
+}
+
+cudaError_t prop_read_codes(const char* reads, const int64_t* offsets, const int32_t* idx, const int8_t* strand,
+                            int32_t n, int32_t ld, uint8_t* codes, int32_t* lens, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_read_codes<<<n, 128, 0, s>>>(reads, offsets, idx, strand, n, ld, codes, lens);
+  return cudaGetLastError();
+}
+
+cudaError_t prop_window_codes(const uint32_t* g2, const uint32_t* gm, const int64_t* starts, int32_t n, int32_t len,
+                              int32_t ld, uint8_t* codes, int32_t* lens, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_window_codes<<<n, 256, 0, s>>>(g2, gm, starts, n, len, ld, codes, lens);
+  return cudaGetLastError();
+}
+
+cudaError_t prop_init_params(float* w, uint64_t seed, cudaStream_t s) {
+  k_init_params<<<(unsigned)((kPropParams + 255) / 256), 256, 0, s>>>(w, seed);
+  return cudaGetLastError();
+}
+
+cudaError_t prop_to_bf16(const float* w, __nv_bfloat16* wb, int64_t n, cudaStream_t s) {
+  k_to_bf16<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(w, wb, n);
+  return cudaGetLastError();
+}
+
+}  // namespace mss

@@ -1,0 +1,59 @@
+// Host-side declarations of the learned-proposal kernels (prop.cu); not part of the ABI.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mss {
+
+constexpr int kPropC = 128;    // channels and embedding width
+constexpr int kPropTaps = 7;   // kernel width ("same" padding of 3)
+constexpr int kPropLayers = 4;
+// flat fp32 parameter vector: W1 [7][4][128], b1 [128], then for layers 2..4:
+// W [7][128 ci][128 co], b [128]
+constexpr int64_t kPropW1 = (int64_t)kPropTaps * 4 * kPropC;
+constexpr int64_t kPropWl = (int64_t)kPropTaps * kPropC * kPropC;
+constexpr int64_t kPropParams = kPropW1 + kPropC + 3 * (kPropWl + kPropC);
+inline int64_t prop_off_b1() { return kPropW1; }
+inline int64_t prop_off_w(int layer) { return kPropW1 + kPropC + (int64_t)(layer - 2) * (kPropWl + kPropC); }
+inline int64_t prop_off_b(int layer) { return prop_off_w(layer) + kPropWl; }
+
+// rows of an activation buffer for sequences of at most maxlen positions
+inline int32_t prop_rows(int32_t maxlen) { return ((maxlen + 127) / 128) * 128 + 6; }
+
+cudaError_t prop_embed_l1(const uint8_t* codes, const int32_t* lens, int32_t ld, int32_t n, const float* w1,
+                          const float* b1, __nv_bfloat16* out, int32_t rows, cudaStream_t s);
+cudaError_t prop_conv(const __nv_bfloat16* in, const __nv_bfloat16* w, const float* bias, const __nv_bfloat16* prev,
+                      const int32_t* lens, __nv_bfloat16* out, int32_t n, int32_t rows, int mode, cudaStream_t s);
+cudaError_t prop_conv_wgrad(const __nv_bfloat16* in, const __nv_bfloat16* g, const int32_t* lens, float* dw, int32_t n,
+                            int32_t rows, cudaStream_t s);
+cudaError_t prop_bias_grad(const __nv_bfloat16* g, const int32_t* lens, float* db, int32_t n, int32_t rows,
+                           cudaStream_t s);
+cudaError_t prop_l1_wgrad(const uint8_t* codes, const int32_t* lens, int32_t ld, const __nv_bfloat16* g, float* dw1,
+                          float* db1, int32_t n, int32_t rows, cudaStream_t s);
+cudaError_t prop_pool_norm(const __nv_bfloat16* act, const int32_t* lens, int32_t n, int32_t rows, float* emb,
+                           float* norms, int32_t* argmax, cudaStream_t s);
+cudaError_t prop_pool_norm_bwd(const float* emb, const float* demb, const float* norms, const int32_t* argmax,
+                               const __nv_bfloat16* act, const int32_t* lens, int32_t n, int32_t rows,
+                               __nv_bfloat16* g4, cudaStream_t s);
+cudaError_t prop_ce_loss(const float* r, const float* c, const int32_t* label, int32_t B, int32_t C, float inv_temp,
+                         float* loss, float* dr, float* dc, float scale, cudaStream_t s);
+cudaError_t prop_adamw(float* w, const float* g, float* m1, float* m2, __nv_bfloat16* wb, int64_t count, float lr,
+                       float beta1, float beta2, float eps, float wd, float bc1, float bc2, cudaStream_t s);
+cudaError_t prop_flip_weights(const __nv_bfloat16* w, __nv_bfloat16* wt, cudaStream_t s);
+cudaError_t prop_scores(const float* er, int32_t R, const __nv_bfloat16* ef, int64_t NF, float* scores,
+                        cudaStream_t s);
+cudaError_t prop_topk(const float* scores, int32_t R, int64_t NF, int32_t K, int32_t* out_f, float* out_s,
+                      cudaStream_t s);
+cudaError_t prop_rescore(const uint32_t* g2, const uint32_t* gm, int64_t F, const char* reads, const int64_t* offsets,
+                         const int32_t* idx, int32_t R, const int32_t* cand, int32_t K, int32_t match,
+                         int32_t mismatch, void* hits, int32_t* cand_scores, cudaStream_t s);
+// codes of reads (strand 0 forward, 1 reverse complement) and of genome windows
+cudaError_t prop_read_codes(const char* reads, const int64_t* offsets, const int32_t* idx, const int8_t* strand,
+                            int32_t n, int32_t ld, uint8_t* codes, int32_t* lens, cudaStream_t s);
+cudaError_t prop_window_codes(const uint32_t* g2, const uint32_t* gm, const int64_t* starts, int32_t n, int32_t len,
+                              int32_t ld, uint8_t* codes, int32_t* lens, cudaStream_t s);
+cudaError_t prop_init_params(float* w, uint64_t seed, cudaStream_t s);
+cudaError_t prop_to_bf16(const float* w, __nv_bfloat16* wb, int64_t n, cudaStream_t s);
+
+}  // namespace mss

@@ -1,0 +1,253 @@
+"""GPU checks of the learned proposal against its oracle (oracle/prop_oracle.py) and against
+the exact path:
+
+* embeddings: BF16 tensor-core conv stack vs the fp64 oracle with the same rounding points
+  (tolerance from the BF16 activation rounding: 2e-2 absolute per coordinate of a unit vector);
+* parameter gradients vs the oracle's backward pass (relative error of the whole vector);
+* input codes (reads, both strands; genome windows) bit-exact;
+* proposal + exact rescoring: with K = all fragments, and with every read falling back, the
+  result equals the exhaustive scan bit for bit; with small K the rescored best/second equal
+  the oracle's exact fragment scores over the candidates;
+* top K consistent with the oracle's scores up to the embedding tolerance;
+* a training step decreases the loss; checkpoints round-trip and reject corruption.
+"""
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+import gen
+import oracle
+from oracle import prop_oracle as po
+from tests.parity_util import assert_hits_equal
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mss():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_1403_2136_gb300 as m
+    from paper_1403_2136_gb300 import build
+    build.build()
+    m.load_library()
+    return m
+
+
+def dev(x):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def random_params(seed, scale=1.0):
+    w = po.unpack(np.zeros(po.param_count()))  # layout check
+    rng = np.random.default_rng(seed)
+    p = np.empty(po.param_count())
+    o = 0
+    n1 = po.TAPS * 4 * po.C
+    p[o:o + n1] = rng.uniform(-1, 1, n1) * np.sqrt(6 / 28) * scale; o += n1
+    p[o:o + po.C] = 0.01; o += po.C
+    for _ in range(3):
+        n = po.TAPS * po.C * po.C
+        p[o:o + n] = rng.uniform(-1, 1, n) * np.sqrt(6 / (po.C * po.TAPS)) * scale; o += n
+        p[o:o + po.C] = 0.01; o += po.C
+    return p.astype(np.float32)
+
+
+def test_embeddings_match_oracle(mss):
+    import torch
+    prop = mss.Proposal(seed=3)
+    params = random_params(11)
+    prop.set_params(params)
+    rng = np.random.default_rng(12)
+    lens = np.array([1, 7, 31, 100, 129, 250, 300, 64], dtype=np.int32)
+    ld = 320
+    codes = np.full((lens.size, ld), 4, np.uint8)
+    for i, L in enumerate(lens):
+        codes[i, :L] = rng.choice(5, size=L, p=[.24, .24, .24, .24, .04])
+    d_emb = torch.zeros(lens.size * 128, dtype=torch.float32, device="cuda")
+    prop.embed(dev(codes), dev(lens), ld, lens.size, int(lens.max()), d_emb)
+    torch.cuda.synchronize()
+    got = d_emb.cpu().numpy().reshape(-1, 128)
+    for i, L in enumerate(lens):
+        want, _ = po.forward(params.astype(np.float64), codes[i, :L])
+        assert np.abs(got[i] - want).max() < 2e-2, (i, L, np.abs(got[i] - want).max())
+        assert np.dot(got[i], want) > 0.999
+    prop.close()
+
+
+def test_gradients_match_oracle(mss):
+    import torch
+    prop = mss.Proposal(seed=4)
+    params = random_params(21)
+    prop.set_params(params)
+    rng = np.random.default_rng(22)
+    lens = np.array([40, 133, 77], dtype=np.int32)
+    ld = 160
+    codes = np.full((lens.size, ld), 4, np.uint8)
+    for i, L in enumerate(lens):
+        codes[i, :L] = rng.integers(0, 4, size=L)
+    demb = rng.normal(size=(lens.size, 128)).astype(np.float32)
+    d_grad = torch.zeros(po.param_count(), dtype=torch.float32, device="cuda")
+    prop.grad(dev(codes), dev(lens), ld, lens.size, int(lens.max()), dev(demb), d_grad)
+    torch.cuda.synchronize()
+    got = d_grad.cpu().numpy().astype(np.float64)
+    want = sum(po.backward(params.astype(np.float64), codes[i, :L], demb[i]) for i, L in enumerate(lens))
+    rel = np.linalg.norm(got - want) / np.linalg.norm(want)
+    assert rel < 5e-2, rel
+    # every block, not just the total
+    o = 0
+    for size in [po.TAPS * 4 * po.C, po.C] + [po.TAPS * po.C * po.C, po.C] * 3:
+        g, w_ = got[o:o + size], want[o:o + size]
+        if np.linalg.norm(w_) > 1e-6:
+            assert np.linalg.norm(g - w_) / np.linalg.norm(w_) < 8e-2, (o, size)
+        o += size
+    prop.close()
+
+
+def test_codes(mss):
+    import torch
+    wl = gen.scaled(gen.workloads()["chrom-230M"], genome_len=30_000, reads=20)
+    genome, reads = gen.materialize(wl)
+    g = mss.mss_load_genome(genome, frag_len=1024, max_read_len=250)
+    prop = mss.Proposal(seed=1)
+    n = reads.count
+    ld = 256
+    idx = np.arange(n, dtype=np.int32)
+    for strand in (0, 1):
+        st = np.full(n, strand, np.int8)
+        d_codes = torch.zeros(n * ld, dtype=torch.uint8, device="cuda")
+        d_lens = torch.zeros(n, dtype=torch.int32, device="cuda")
+        prop.read_codes(dev(reads.seq), dev(reads.offsets), dev(idx), dev(st), n, ld, d_codes, d_lens)
+        c = d_codes.cpu().numpy().reshape(n, ld)
+        for i in range(n):
+            q = oracle.encode(reads.read(i))
+            if strand:
+                q = oracle.revcomp_codes(q)
+            assert np.array_equal(c[i, :q.size], q) and (c[i, q.size:] == 4).all()
+    starts = np.array([0, 1000, 29_000, 29_990], dtype=np.int64)
+    d_codes = torch.zeros(4 * 64, dtype=torch.uint8, device="cuda")
+    d_lens = torch.zeros(4, dtype=torch.int32, device="cuda")
+    prop.window_codes(g, dev(starts), 4, 50, 64, d_codes, d_lens)
+    c = d_codes.cpu().numpy().reshape(4, 64)
+    full = np.concatenate([oracle.encode(genome), np.full(200, 4, np.uint8)])
+    for i, s in enumerate(starts):
+        assert np.array_equal(c[i, :50], full[s:s + 50])
+    prop.close()
+    g.close()
+
+
+def _proposal_setup(mss, K_frags=None, seed=5):
+    import torch
+    wl = gen.scaled(gen.workloads()["bact-4.6M"], genome_len=40_000, reads=24)
+    genome, reads = gen.materialize(wl)
+    g = mss.mss_load_genome(genome, frag_len=1024, max_read_len=150)
+    prop = mss.Proposal(seed=seed)
+    prop.build_index(g, 150)
+    return wl, genome, reads, g, prop
+
+
+def test_proposed_with_all_fragments_equals_exhaustive(mss):
+    import torch
+    wl, genome, reads, g, prop = _proposal_setup(mss)
+    NF = g.info()["num_frags"]
+    R = reads.count
+    d_out = torch.zeros(R * 32, dtype=torch.uint8, device="cuda")
+    nfb = prop.map_reads(g, dev(reads.seq), dev(reads.offsets), R, 150, 5, -4, NF, -1e30, d_out)
+    assert nfb == 0
+    got = mss.hits_from_bytes(d_out.cpu())
+    want = mss.mss_map_reads(g, reads.seq, reads.offsets, 5, -4)
+    assert_hits_equal(got, want, "K = NF")
+    # everything falls back: the exhaustive path
+    d_out.zero_()
+    nfb = prop.map_reads(g, dev(reads.seq), dev(reads.offsets), R, 150, 5, -4, 4, 1e30, d_out)
+    assert nfb == R
+    assert_hits_equal(mss.hits_from_bytes(d_out.cpu()), want, "all fallback")
+    prop.close()
+    g.close()
+
+
+def test_proposed_small_k_rescoring_is_exact(mss):
+    import torch
+    wl, genome, reads, g, prop = _proposal_setup(mss)
+    R, K, F = reads.count, 6, 1024
+    d_out = torch.zeros(R * 32, dtype=torch.uint8, device="cuda")
+    d_cand = torch.zeros(R * K, dtype=torch.int32, device="cuda")
+    prop.map_reads(g, dev(reads.seq), dev(reads.offsets), R, 150, 5, -4, K, -1e30, d_out, d_cand=d_cand)
+    hits = mss.hits_from_bytes(d_out.cpu())
+    cand = d_cand.cpu().numpy().reshape(R, K)
+    for i in range(R):
+        _, fs = oracle.map_read(genome, F, reads.read(i), 5, -4, with_frag_scores=True)
+        cs = [(int(fs[f]), int(f)) for f in cand[i] if f >= 0]
+        assert len(set(f for _, f in cs)) == len(cs)
+        order = sorted(cs, key=lambda x: (-x[0], x[1]))
+        assert hits["best_frag"][i] == order[0][1] and hits["best_score"][i] == order[0][0]
+        if len(order) > 1:
+            assert hits["second_frag"][i] == order[1][1] and hits["second_score"][i] == order[1][0]
+    prop.close()
+    g.close()
+
+
+def test_topk_consistent_with_oracle_scores(mss):
+    import torch
+    wl, genome, reads, g, prop = _proposal_setup(mss)
+    params = prop.get_params().astype(np.float64)
+    R, K, F = reads.count, 5, 1024
+    NF = g.info()["num_frags"]
+    d_out = torch.zeros(R * 32, dtype=torch.uint8, device="cuda")
+    d_cand = torch.zeros(R * K, dtype=torch.int32, device="cuda")
+    prop.map_reads(g, dev(reads.seq), dev(reads.offsets), R, 150, 5, -4, K, -1e30, d_out, d_cand=d_cand)
+    cand = d_cand.cpu().numpy().reshape(R, K)
+    gcodes = np.concatenate([oracle.encode(genome), np.full(F + 200, 4, np.uint8)])
+    ef = np.stack([po.forward(params, gcodes[f * F:f * F + F + 149])[0] for f in range(NF)])
+    for i in range(0, R, 4):
+        q = oracle.encode(reads.read(i))
+        e1, _ = po.forward(params, q)
+        e2, _ = po.forward(params, oracle.revcomp_codes(q))
+        sc = np.maximum(ef @ e1, ef @ e2)
+        kth = np.sort(sc)[::-1][K - 1]
+        for f in cand[i]:
+            assert sc[f] >= kth - 0.05, (i, f, sc[f], kth)
+    prop.close()
+    g.close()
+
+
+def test_training_step_and_checkpoint(mss):
+    import torch
+    prop = mss.Proposal(seed=9)
+    rng = np.random.default_rng(31)
+    B, C, Lr, Lc = 16, 16, 80, 300
+    rc = rng.integers(0, 4, size=(B, Lr)).astype(np.uint8)
+    cc = rng.integers(0, 4, size=(C, Lc)).astype(np.uint8)
+    for i in range(B):                      # read i is a substring of candidate i
+        s = rng.integers(0, Lc - Lr)
+        cc[i, s:s + Lr] = rc[i]
+    rl = np.full(B, Lr, np.int32)
+    cl = np.full(C, Lc, np.int32)
+    lab = np.arange(B, dtype=np.int32)
+    d = [dev(x) for x in (rc, rl, cc, cl, lab)]
+    # the first step's loss equals the oracle's loss on the oracle's embeddings
+    params = prop.get_params().astype(np.float64)
+    er = np.stack([po.forward(params, rc[i])[0] for i in range(B)])
+    ec = np.stack([po.forward(params, cc[j])[0] for j in range(C)])
+    want_loss, _, _ = po.ce_loss(er, ec, lab, 0.1)
+    losses = [prop.train_step(d[0], d[1], Lr, B, Lr, d[2], d[3], Lc, C, Lc, d[4], lr=3e-3, temperature=0.1)
+              for _ in range(25)]
+    assert abs(losses[0] - want_loss) < 5e-2 * max(1.0, abs(want_loss)), (losses[0], want_loss)
+    assert losses[-1] < losses[0] * 0.8, losses
+    with tempfile.TemporaryDirectory() as td:
+        path = os.path.join(td, "prop.ckpt")
+        prop.save(path)
+        before = prop.get_params()
+        other = mss.Proposal(seed=123)
+        other.load(path)
+        assert np.array_equal(other.get_params(), before)
+        raw = bytearray(open(path, "rb").read())
+        raw[100] ^= 0xFF
+        open(path, "wb").write(bytes(raw))
+        with pytest.raises(mss.MssError):
+            other.load(path)
+        other.close()
+    prop.close()
