@@ -207,3 +207,18 @@ def test_autotune_keeps_results(mss):
     after = mss.mss_map_reads(g, reads.seq, reads.offsets, 5, -4)
     assert_hits_equal(after, before, "autotune")
     g.close()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_genome_sharding_on_gpu_equals_unsharded(mss, world):
+    """Genome shards mapped one after another on this GPU and merged (the exchange emulated in
+    memory) give the unsharded result bit for bit."""
+    from paper_1403_2136_gb300 import shard
+    wl = gen.scaled(gen.workloads()["bact-4.6M"], genome_len=300_000, reads=60)
+    genome, reads = gen.materialize(wl)
+    ml = int(np.diff(reads.offsets).max())
+    got = shard.map_sharded_local(genome, 2048, reads.seq, reads.offsets, 5, -4, world, ml)
+    g = mss.mss_load_genome(genome, frag_len=2048, max_read_len=ml)
+    want = mss.mss_map_reads(g, reads.seq, reads.offsets, 5, -4)
+    g.close()
+    assert_hits_equal(got, want, f"{world} GPU shards")
