@@ -63,22 +63,6 @@ struct DevBuf {
   }
 };
 
-// f16 bit pattern of a small integer (|x| <= 2048), built from the IEEE half layout.
-uint32_t int_to_f16_bits(int32_t x) {
-  if (x == 0) return 0;
-  uint32_t sign = x < 0 ? 0x8000u : 0u;
-  uint32_t v = (uint32_t)(x < 0 ? -x : x);
-  int e = 31 - __builtin_clz(v);  // v = 1.f * 2^e
-  uint32_t mant = (e >= 10) ? ((v >> (e - 10)) & 0x3FFu) : ((v << (10 - e)) & 0x3FFu);
-  return sign | ((uint32_t)(e + 15) << 10) | mant;
-}
-
-bool f16_path_exact(int32_t max_len, int32_t match, int32_t mismatch) {
-  if ((int64_t)max_len * match > 2048) return false;  // every partial sum is an integer <= 2048
-  if (match > 2048 || mismatch < -2048) return false;
-  return (int_to_f16_bits(match) & 0xFFu) == 0 && (int_to_f16_bits(mismatch) & 0xFFu) == 0;
-}
-
 struct GraphKey {
   const void* reads;
   const void* offsets;
@@ -439,6 +423,23 @@ mss_status stage_reads(mss_ctx* c, const char* reads, const int64_t* offsets, in
 }  // namespace
 
 namespace mss {
+
+// f16 bit pattern of a small integer (|x| <= 2048), built from the IEEE half layout.
+uint32_t int_to_f16_bits(int32_t x) {
+  if (x == 0) return 0;
+  uint32_t sign = x < 0 ? 0x8000u : 0u;
+  uint32_t v = (uint32_t)(x < 0 ? -x : x);
+  int e = 31 - __builtin_clz(v);  // v = 1.f * 2^e
+  uint32_t mant = (e >= 10) ? ((v >> (e - 10)) & 0x3FFu) : ((v << (10 - e)) & 0x3FFu);
+  return sign | ((uint32_t)(e + 15) << 10) | mant;
+}
+
+bool f16_path_exact(int32_t max_len, int32_t match, int32_t mismatch) {
+  if ((int64_t)max_len * match > 2048) return false;  // every partial sum is an integer <= 2048
+  if (match > 2048 || mismatch < -2048) return false;
+  return (int_to_f16_bits(match) & 0xFFu) == 0 && (int_to_f16_bits(mismatch) & 0xFFu) == 0;
+}
+
 
 bool ctx_view(mss_ctx* c, CtxView* v) {
   if (!c || !v) return false;

@@ -156,4 +156,38 @@ __device__ __forceinline__ Top2 top2_shfl_xor(Top2 v, int mask) {
 
 __device__ __forceinline__ Top2 top2_empty() { return Top2{-1, 0x7fffffff, -1, 0x7fffffff}; }
 
+// ---- packed-lane maximum-scoring-subsequence step (scan and candidate rescoring)
+// PRMT selector for the lane pair (genome code c1 at d + k, code c2 at d + D + k).
+template <bool F16>
+__device__ __forceinline__ uint32_t make_sel(uint32_t c1, uint32_t c2) {
+  if (F16) {
+    // f16 lane = [low byte 0x00 (byte 4 of {b,a}), high byte = profile byte c, or byte 5 for N]
+    uint32_t n1 = c1 < 4 ? c1 : 5u, n2 = c2 < 4 ? c2 : 5u;
+    return 4u | (n1 << 4) | (4u << 8) | (n2 << 12);
+  } else {
+    // int16 lane = [profile byte c (byte 4 = mismatch for N), its sign replicated]
+    uint32_t n1 = c1 < 4 ? c1 : 4u, n2 = c2 < 4 ? c2 : 4u;
+    return n1 | ((n1 | 8u) << 4) | (n2 << 8) | ((n2 | 8u) << 12);
+  }
+}
+
+// Profile word of one query base: byte b = score byte of (query base, genome base b).
+__device__ __forceinline__ uint32_t profile_word(uint32_t code, uint32_t ma, uint32_t mm) {
+  uint32_t w = mm * 0x01010101u;
+  if (code < 4) w = (w & ~(0xFFu << (8 * code))) | (ma << (8 * code));
+  return w;
+}
+
+template <bool F16>
+__device__ __forceinline__ uint32_t kadane_step(uint32_t h, uint32_t s) {
+  if (F16) return hfma2_relu(h, 0x3C003C00u, s);   // relu(h * 1 + s) on two f16 lanes
+  return __viaddmax_s16x2(h, s, 0u);                // max(h + s, 0) on two int16 lanes
+}
+
+template <bool F16>
+__device__ __forceinline__ int32_t lane_value(uint32_t bits16) {
+  if (F16) return f16_bits_to_int(bits16);
+  return (int32_t)(int16_t)(bits16 & 0xFFFFu);
+}
+
 }  // namespace mss

@@ -18,13 +18,14 @@
 //   k_adamw         AdamW on FP32 master weights, refreshing the BF16 copies
 //   k_scores        read x fragment scores (max over the read's two strands)
 //   k_topk          per-read top K (ties -> lower fragment), by 4-round radix select
-//   k_rescore       exact MSS of each read on its K candidate fragments, top-2 among them
+// (the exact rescoring of the candidates is in rescore.cu)
 #include <cuda_bf16.h>
 
 #include "../../include/maxss.h"
 #include "common.cuh"
 #include "internal.h"
 #include "prop.h"
+#include "tc.cuh"
 
 namespace mss {
 
@@ -451,6 +452,7 @@ __global__ void k_flip_weights(const __nv_bfloat16* __restrict__ w, __nv_bfloat1
 
 // ------------------------------------------------------------------------------------------
 // scores[i][f] = max(<e_fwd_i, e_f>, <e_rev_i, e_f>); a CTA takes 8 reads x 128 fragments
+// (CUDA cores, FP32 read embeddings; used for K above the tensor-core path's 128)
 __global__ void k_scores(const float* __restrict__ er, int32_t R, const __nv_bfloat16* __restrict__ ef, int64_t NF,
                          float* __restrict__ scores) {
   __shared__ float s_e[16][kPropC];
@@ -466,9 +468,11 @@ __global__ void k_scores(const float* __restrict__ er, int32_t R, const __nv_bfl
   float acc[16];
 #pragma unroll
   for (int q = 0; q < 16; ++q) acc[q] = 0.f;
-  const __nv_bfloat162* fr = reinterpret_cast<const __nv_bfloat162*>(ef + f * kPropC);
+  // the index is stored as canonical tensor-core tiles of 128 fragments (tc.cuh)
+  const uint8_t* ft = reinterpret_cast<const uint8_t*>(ef) + (f >> 7) * (int64_t)(128 * kPropC * 2);
   for (int k2 = 0; k2 < kPropC / 2; ++k2) {
-    const float2 v = __bfloat1622float2(fr[k2]);
+    const float2 v = __bfloat1622float2(
+        *reinterpret_cast<const __nv_bfloat162*>(ft + canon_offset((uint32_t)(f & 127), (uint32_t)(2 * k2))));
 #pragma unroll
     for (int q = 0; q < 16; ++q) acc[q] += s_e[q][2 * k2] * v.x + s_e[q][2 * k2 + 1] * v.y;
   }
@@ -596,104 +600,6 @@ __global__ void k_topk(const float* __restrict__ scores, int64_t NF, int32_t K, 
 }
 
 // ------------------------------------------------------------------------------------------
-// exact rescoring: one warp per read; for each of its K candidate fragments the MSS of every
-// diagonal on both strands (int32, the plain recurrence), the fragment maximum, and the top-2
-// among the candidates (ties -> lower fragment) with the best diagonal (ties: + strand, then
-// smaller d).  Writes an mss_hit per read (second fragment / score among the candidates).
-constexpr int kRsWarps = 4;
-constexpr int kRsChunk = 512;
-
-__global__ void __launch_bounds__(kRsWarps * 32)
-    k_rescore(const uint32_t* __restrict__ g2, const uint32_t* __restrict__ gm, int64_t F, const char* __restrict__ reads,
-              const int64_t* __restrict__ offsets, const int32_t* __restrict__ idx, int32_t R,
-              const int32_t* __restrict__ cand, int32_t K, int32_t match, int32_t mismatch, void* hits,
-              int32_t* __restrict__ cand_scores) {
-  __shared__ uint8_t s_gen[kRsWarps][kRsChunk + MSS_MAX_READ_LEN + 16];
-  __shared__ uint8_t s_q[kRsWarps][2][MSS_MAX_READ_LEN];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int i = blockIdx.x * kRsWarps + wib;
-  if (i >= R) return;
-  const int ridx = idx ? idx[i] : i;
-  const int64_t off = offsets[ridx];
-  int64_t l = offsets[ridx + 1] - off;
-  const int32_t m = l < 0 ? 0 : (l > MSS_MAX_READ_LEN ? MSS_MAX_READ_LEN : (int32_t)l);
-  for (int k = lane; k < m; k += 32) {
-    uint32_t cf = ascii_code((uint8_t)reads[off + k]);
-    if (cf > 4) cf = 4;
-    s_q[wib][0][k] = (uint8_t)cf;
-    s_q[wib][1][m - 1 - k] = (uint8_t)(cf < 4 ? 3 - cf : 4);
-  }
-  __syncwarp();
-  int32_t s1 = -1, f1 = 0x7fffffff, s2 = -1, f2 = 0x7fffffff, bS = 0;
-  int64_t bD = 0;
-  for (int c = 0; c < K; ++c) {
-    const int32_t f = cand[(int64_t)i * K + c];
-    if (f < 0) continue;
-    int32_t bestK = -1, bestS = 0;
-    int64_t bestD = 0;
-    const int64_t d_lo = (int64_t)f * F, d_hi = d_lo + F;
-    for (int sg = 0; sg < 2; ++sg) {
-      for (int64_t d0 = d_lo; d0 < d_hi; d0 += kRsChunk) {
-        const int64_t nd = (d_hi - d0 < (int64_t)kRsChunk) ? d_hi - d0 : (int64_t)kRsChunk;
-        __syncwarp();
-        for (int64_t x = lane; x < nd + m; x += 32) s_gen[wib][x] = (uint8_t)genome_code(g2, gm, d0 + x);
-        __syncwarp();
-        for (int64_t x = lane; x < nd; x += 32) {
-          int32_t h = 0, mx = 0;
-          for (int k = 0; k < m; ++k) {
-            const uint32_t qc = s_q[wib][sg][k], gc = s_gen[wib][x + k];
-            h += (qc < 4 && qc == gc) ? match : mismatch;
-            h = max(h, 0);
-            mx = max(mx, h);
-          }
-          if (mx > bestK) {
-            bestK = mx;
-            bestS = sg;
-            bestD = d0 + x;
-          }
-        }
-      }
-    }
-#pragma unroll
-    for (int s = 16; s > 0; s >>= 1) {
-      const int32_t oK = __shfl_xor_sync(0xffffffffu, bestK, s);
-      const int32_t oS = __shfl_xor_sync(0xffffffffu, bestS, s);
-      const int64_t oD = __shfl_xor_sync(0xffffffffu, bestD, s);
-      if (oK > bestK || (oK == bestK && (oS < bestS || (oS == bestS && oD < bestD)))) {
-        bestK = oK;
-        bestS = oS;
-        bestD = oD;
-      }
-    }
-    if (cand_scores && lane == 0) cand_scores[(int64_t)i * K + c] = bestK;
-    // top-2 over candidates (distinct fragments; the list may repeat none)
-    if (bestK > s1 || (bestK == s1 && f < f1)) {
-      s2 = s1;
-      f2 = f1;
-      s1 = bestK;
-      f1 = f;
-      bS = bestS;
-      bD = bestD;
-    } else if (f != f1 && (bestK > s2 || (bestK == s2 && f < f2))) {
-      s2 = bestK;
-      f2 = f;
-    }
-  }
-  if (lane == 0) {
-    mss_hit h;
-    h.best_frag = s1 < 0 ? -1 : f1;
-    h.best_score = s1 < 0 ? 0 : s1;
-    h.second_frag = s2 < 0 ? -1 : f2;
-    h.second_score = s2 < 0 ? 0 : s2;
-    h.offset = bD;
-    h.strand = bS;
-    const bool repeat = (h.best_score == 0) || (10LL * h.second_score >= 9LL * h.best_score);
-    h.flags = repeat ? MSS_HIT_REPEAT : 0;
-    reinterpret_cast<mss_hit*>(hits)[i] = h;
-  }
-}
-
-// ------------------------------------------------------------------------------------------
 // host launchers
 cudaError_t prop_embed_l1(const uint8_t* codes, const int32_t* lens, int32_t ld, int32_t n, const float* w1,
                           const float* b1, __nv_bfloat16* out, int32_t rows, cudaStream_t s) {
@@ -787,14 +693,6 @@ cudaError_t prop_topk(const float* scores, int32_t R, int64_t NF, int32_t K, int
   return cudaGetLastError();
 }
 
-cudaError_t prop_rescore(const uint32_t* g2, const uint32_t* gm, int64_t F, const char* reads, const int64_t* offsets,
-                         const int32_t* idx, int32_t R, const int32_t* cand, int32_t K, int32_t match,
-                         int32_t mismatch, void* hits, int32_t* cand_scores, cudaStream_t s) {
-  if (R <= 0) return cudaSuccess;
-  k_rescore<<<(R + kRsWarps - 1) / kRsWarps, kRsWarps * 32, 0, s>>>(g2, gm, F, reads, offsets, idx, R, cand, K, match,
-                                                                     mismatch, hits, cand_scores);
-  return cudaGetLastError();
-}
 
 }  // namespace mss
 

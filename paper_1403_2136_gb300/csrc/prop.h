@@ -45,9 +45,27 @@ cudaError_t prop_scores(const float* er, int32_t R, const __nv_bfloat16* ef, int
                         cudaStream_t s);
 cudaError_t prop_topk(const float* scores, int32_t R, int64_t NF, int32_t K, int32_t* out_f, float* out_s,
                       cudaStream_t s);
+// a9 on the tensor cores (score_tc.cu).  The fragment index is stored as BF16 tiles of 128
+// fragments in the canonical K-major operand layout (tc.cuh); read embeddings are packed the
+// same way in blocks of 128 sequences (forward, reverse complement of each read).
+int64_t prop_index_bytes(int64_t NF);
+int64_t prop_read_block_bytes(int32_t R);
+cudaError_t prop_store_index(const float* emb, int64_t f0, int32_t nb, void* index, cudaStream_t s);
+cudaError_t prop_pack_reads(const float* er, int32_t R, void* out, cudaStream_t s);
+// fragment splits per block of 64 reads (at least one CTA per SM; S * K <= 256)
+int32_t prop_score_splits(int32_t R, int64_t NF, int32_t K, int num_sms);
+// per read the K <= 128 best fragments (score desc, fragment asc) into out_f / out_s [R][K];
+// part_key / part_f: [S][R][K] workspace when S > 1
+cudaError_t prop_score_topk(const void* breads, int32_t R, const void* index, int64_t NF, int32_t K, int32_t S,
+                            int32_t* out_f, float* out_s, uint32_t* part_key, int32_t* part_f, int32_t* err,
+                            cudaStream_t s);
+// exact rescoring of K candidate fragments per read (rescore.cu): per-candidate maxima with the
+// packed-lane scan, then the top-2 among the candidates and the best diagonal.  Reads longer
+// than max_len set ERR_BAD_LEN in *err and are cut to max_len.
 cudaError_t prop_rescore(const uint32_t* g2, const uint32_t* gm, int64_t F, const char* reads, const int64_t* offsets,
-                         const int32_t* idx, int32_t R, const int32_t* cand, int32_t K, int32_t match,
-                         int32_t mismatch, void* hits, int32_t* cand_scores, cudaStream_t s);
+                         const int32_t* idx, int32_t R, int32_t max_len, const int32_t* cand, int32_t K,
+                         int32_t match, int32_t mismatch, void* hits, int32_t* cand_scores, int32_t* err,
+                         int num_sms, cudaStream_t s);
 // codes of reads (strand 0 forward, 1 reverse complement) and of genome windows
 cudaError_t prop_read_codes(const char* reads, const int64_t* offsets, const int32_t* idx, const int8_t* strand,
                             int32_t n, int32_t ld, uint8_t* codes, int32_t* lens, cudaStream_t s);

@@ -1,6 +1,6 @@
 // C ABI of the learned fragment proposal: model state, training step, fragment index,
 // proposal-then-exact mapping with exhaustive fallback, checkpoints.  Argument checks and
-// orchestration only; the compute is in prop.cu and scan.cu.
+// orchestration only; the compute is in prop.cu, rescore.cu and scan.cu.
 #include <cuda_bf16.h>
 #include <stdio.h>
 #include <string.h>
@@ -78,7 +78,7 @@ struct mss_prop {
   int64_t index_nf = 0, index_F = 0;
   int32_t index_window = 0;
   const void* index_genome = nullptr;
-  Buf scores, cand, cand_s, emb_reads;
+  Buf scores, cand, cand_s, cand_x, emb_reads, breads, part_key, part_f;
   int64_t step = 0;
   int64_t launches = 0;
 };
@@ -199,7 +199,8 @@ mss_status mss_prop_create(mss_prop** out, uint64_t seed, void* stream) {
 void mss_prop_free(mss_prop* p) {
   if (!p) return;
   for (Buf* b : {&p->w32, &p->m1, &p->m2, &p->grad, &p->loss, &p->de_r, &p->de_c, &p->codes, &p->lens, &p->starts,
-                 &p->idx, &p->strand, &p->index, &p->scores, &p->cand, &p->cand_s, &p->emb_reads, &p->g[0], &p->g[1]})
+                 &p->idx, &p->strand, &p->index, &p->scores, &p->cand, &p->cand_s, &p->emb_reads, &p->g[0], &p->g[1],
+                 &p->cand_x, &p->breads, &p->part_key, &p->part_f})
     b->release();
   for (int l = 0; l < 3; ++l) {
     p->wb[l].release();
@@ -311,7 +312,8 @@ mss_status mss_prop_build_index(mss_prop* p, mss_ctx* ctx, int32_t max_read_len,
   const int64_t NF = gi.num_frags, F = gi.frag_len;
   const int32_t win = (int32_t)(F + max_read_len - 1);
   if (win > 65536) return set_error(MSS_EINVAL, "fragment window above 65536 bases");
-  PCK(p->index.ensure((size_t)NF * kPropC * 2), "index");
+  PCK(p->index.ensure((size_t)prop_index_bytes(NF)), "index");
+  PCK(cudaMemsetAsync(p->index.p, 0, (size_t)prop_index_bytes(NF), s), "index clear");
   // batches of fragments bounded by ~1 GB of activations
   const int32_t rows = prop_rows(win);
   int32_t batch = (int32_t)std::max<int64_t>(1, (int64_t)(1u << 30) / ((int64_t)rows * kPropC * 2 * 4));
@@ -334,8 +336,7 @@ mss_status mss_prop_build_index(mss_prop* p, mss_ctx* ctx, int32_t max_read_len,
       tmp.release();
       return st;
     }
-    PCK(prop_to_bf16(p->fa.emb.as<float>(), p->index.as<__nv_bfloat16>() + f0 * kPropC, (int64_t)nb * kPropC, s),
-        "index store");
+    PCK(prop_store_index(p->fa.emb.as<float>(), f0, nb, p->index.p, s), "index store");
     PCK(cudaStreamSynchronize(s), "sync");  // hs is reused
     p->launches += 2;
   }
@@ -397,31 +398,50 @@ mss_status mss_map_reads_proposed(mss_ctx* ctx, mss_prop* p, const char* d_reads
                         cudaMemcpyDeviceToDevice, s),
         "embedding copy");
   }
-  // scores and top K in read batches bounded by ~2 GB of scores
-  int32_t rb = (int32_t)std::max<int64_t>(1, std::min<int64_t>(R, (int64_t)(2ll << 30) / (NF * 4)));
-  PCK(p->scores.ensure((size_t)rb * NF * 4), "scores");
   PCK(p->cand.ensure((size_t)R * K * 4), "candidates");
   PCK(p->cand_s.ensure((size_t)R * K * 4), "candidate scores");
-  for (int32_t a = 0; a < R; a += rb) {
-    const int32_t nb = std::min(rb, R - a);
-    PCK(prop_scores(p->emb_reads.as<float>() + (size_t)a * 2 * kPropC, nb, p->index.as<__nv_bfloat16>(), NF,
-                    p->scores.as<float>(), s),
-        "scores");
-    PCK(prop_topk(p->scores.as<float>(), nb, NF, K, p->cand.as<int32_t>() + (size_t)a * K,
-                  p->cand_s.as<float>() + (size_t)a * K, s),
-        "top K");
-    p->launches += 2;
+  if (K <= 128) {
+    // tensor cores: scores and the streaming top K fused, nothing of size R x NF stored
+    PCK(p->breads.ensure((size_t)prop_read_block_bytes(R)), "read blocks");
+    PCK(prop_pack_reads(p->emb_reads.as<float>(), R, p->breads.p, s), "read pack");
+    const int32_t S = prop_score_splits(R, NF, K, v.num_sms);
+    if (S > 1) {
+      PCK(p->part_key.ensure((size_t)S * R * K * 4), "split lists");
+      PCK(p->part_f.ensure((size_t)S * R * K * 4), "split lists");
+    }
+    PCK(prop_score_topk(p->breads.p, R, p->index.p, NF, K, S, p->cand.as<int32_t>(), p->cand_s.as<float>(),
+                        p->part_key.as<uint32_t>(), p->part_f.as<int32_t>(), v.d_err, s),
+        "scores and top K");
+    p->launches += S > 1 ? 3 : 2;
+  } else {
+    // CUDA cores: scores in read batches bounded by ~2 GB, then a radix top K
+    int32_t rb = (int32_t)std::max<int64_t>(1, std::min<int64_t>(R, (int64_t)(2ll << 30) / (NF * 4)));
+    PCK(p->scores.ensure((size_t)rb * NF * 4), "scores");
+    for (int32_t a = 0; a < R; a += rb) {
+      const int32_t nb = std::min(rb, R - a);
+      PCK(prop_scores(p->emb_reads.as<float>() + (size_t)a * 2 * kPropC, nb, p->index.as<__nv_bfloat16>(), NF,
+                      p->scores.as<float>(), s),
+          "scores");
+      PCK(prop_topk(p->scores.as<float>(), nb, NF, K, p->cand.as<int32_t>() + (size_t)a * K,
+                    p->cand_s.as<float>() + (size_t)a * K, s),
+          "top K");
+      p->launches += 2;
+    }
   }
   // exact rescoring of the candidates
-  PCK(prop_rescore(v.g2, v.gm, p->index_F, d_reads, d_offsets, nullptr, R, p->cand.as<int32_t>(), K, sp->match,
-                   sp->mismatch, d_out, nullptr, s),
+  PCK(p->cand_x.ensure((size_t)R * K * 4), "candidate maxima");
+  PCK(prop_rescore(v.g2, v.gm, p->index_F, d_reads, d_offsets, nullptr, R, max_len, p->cand.as<int32_t>(), K,
+                   sp->match, sp->mismatch, d_out, p->cand_x.as<int32_t>(), v.d_err, v.num_sms, s),
       "rescore");
-  p->launches += 1;
+  p->launches += 2;
   if (d_cand) PCK(cudaMemcpyAsync(d_cand, p->cand.p, (size_t)R * K * 4, cudaMemcpyDeviceToDevice, s), "cand copy");
   // fallback: reads whose best proposal score is below tau get the exhaustive scan
   std::vector<float> top((size_t)R * K);
   PCK(cudaMemcpyAsync(top.data(), p->cand_s.p, (size_t)R * K * 4, cudaMemcpyDeviceToHost, s), "scores read");
-  PCK(cudaStreamSynchronize(s), "sync");
+  {
+    mss_status est = mss_sync(ctx, stream);  // synchronizes; reports bad characters / lengths
+    if (est) return est;
+  }
   if (d_top_score) {
     std::vector<float> t1(R);
     for (int32_t i = 0; i < R; ++i) t1[i] = top[(size_t)i * K];

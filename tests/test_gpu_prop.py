@@ -190,6 +190,109 @@ def test_proposed_small_k_rescoring_is_exact(mss):
     g.close()
 
 
+@pytest.mark.parametrize("F,match,mismatch", [(3000, 5, -4), (3000, 13, -4), (700, 1, -1)])
+def test_rescoring_exact_multi_pass_fragments(mss, F, match, mismatch):
+    """Candidate rescoring where a fragment takes several 2048-diagonal passes with a ragged
+    last one (F = 3000, not a multiple of 16), where one pass covers less than a fragment
+    (F = 700), with the int16 lanes (13 / -4 has no exact f16 byte form) and the f16 lanes,
+    and with reads holding N and reads of one and two bases."""
+    import torch
+    from tests.parity_util import concat_reads
+    wl = gen.scaled(gen.workloads()["bact-4.6M"], genome_len=30_000, reads=10)
+    genome, reads = gen.materialize(wl)
+    strs = [bytes(reads.read(i)) for i in range(reads.count)]
+    g_ascii = bytes(genome)
+    strs += [g_ascii[5000:5120].replace(b"A", b"N", 7), b"G", b"TA", g_ascii[29_900:30_000]]
+    seq, off = concat_reads(strs)
+    R, K = len(strs), 5
+    g = mss.mss_load_genome(genome, frag_len=F, max_read_len=150)
+    prop = mss.Proposal(seed=9)
+    prop.build_index(g, 150)
+    d_out = torch.zeros(R * 32, dtype=torch.uint8, device="cuda")
+    d_cand = torch.zeros(R * K, dtype=torch.int32, device="cuda")
+    prop.map_reads(g, dev(seq), dev(off), R, 150, match, mismatch, K, -1e30, d_out, d_cand=d_cand)
+    hits = mss.hits_from_bytes(d_out.cpu())
+    cand = d_cand.cpu().numpy().reshape(R, K)
+    for i in range(R):
+        q = np.frombuffer(strs[i], dtype=np.uint8)
+        want, fs = oracle.map_read(genome, F, q, match, mismatch, with_frag_scores=True)
+        cs = sorted([(int(fs[f]), int(f)) for f in cand[i] if f >= 0], key=lambda x: (-x[0], x[1]))
+        assert hits["best_frag"][i] == cs[0][1] and hits["best_score"][i] == cs[0][0], (i, cs, hits[i])
+        assert hits["second_frag"][i] == cs[1][1] and hits["second_score"][i] == cs[1][0], (i, cs, hits[i])
+        # when the candidates hold the exhaustive best fragment, the best diagonal and strand are
+        # the exhaustive scan's (the argmax rule inside one fragment)
+        if want[0] == cs[0][1]:
+            assert hits["offset"][i] == want[4] and hits["strand"][i] == want[5], i
+    prop.close()
+    g.close()
+
+
+@pytest.mark.parametrize("R,K,genome_len", [(100, 64, 150_000), (70, 128, 150_000), (9_800, 64, 66_000),
+                                             (33, 5, 20_000)])
+def test_tensor_core_topk_matches_numpy(mss, R, K, genome_len):
+    """The fused tensor-core scores + streaming top K against numpy on the same BF16
+    embeddings (the GPU's own fp32 embeddings rounded to BF16): every returned fragment is
+    among the K best (within FP32 accumulation error), the list is in score order, and ties
+    between identical embeddings (two fragments with identical windows) go to the lower
+    fragment.  Equal fp64 scores of different embeddings are not ties on the GPU: the FP32
+    accumulation may separate them by an ulp.  Sizes: several
+    fragment splits with the merge (100 reads), K = 128 (70 reads), one split per read block
+    (9,800 reads = 154 blocks of 64), a ragged last tile of 128 fragments, NF below 128."""
+    import torch
+    F, ML = 512, 100
+    wl = gen.scaled(gen.workloads()["chrom-230M"], genome_len=genome_len, reads=R)
+    genome = gen.make_genome(wl.genome, wl.seed).copy()
+    win = F + ML - 1
+    f1, f2 = 3, 17                      # twin fragments: identical windows
+    genome[f2 * F:f2 * F + win] = genome[f1 * F:f1 * F + win]
+    reads = gen.make_reads(genome, gen.ReadSpec(R, lengths=(36, 51, 76, 100), sub_levels=((0.1, 0.2),)), wl.seed + 3)
+    g = mss.mss_load_genome(genome, frag_len=F, max_read_len=ML)
+    NF = g.info()["num_frags"]
+    prop = mss.Proposal(seed=2)
+    prop.build_index(g, ML)
+    d_out = torch.zeros(R * 32, dtype=torch.uint8, device="cuda")
+    d_cand = torch.zeros(R * K, dtype=torch.int32, device="cuda")
+    prop.map_reads(g, dev(reads.seq), dev(reads.offsets), R, ML, 5, -4, K, -1e30, d_out, d_cand=d_cand)
+    cand = d_cand.cpu().numpy().reshape(R, K)
+    # the same embeddings, computed by the library's own forward pass
+    d_codes = torch.zeros(NF * win, dtype=torch.uint8, device="cuda")
+    d_lens = torch.zeros(NF, dtype=torch.int32, device="cuda")
+    prop.window_codes(g, dev(np.arange(NF, dtype=np.int64) * F), NF, win, win, d_codes, d_lens)
+    d_ef = torch.zeros(NF * 128, dtype=torch.float32, device="cuda")
+    prop.embed(d_codes, d_lens, win, NF, win, d_ef)
+    n = 2 * R
+    idx = np.repeat(np.arange(R, dtype=np.int32), 2)
+    st = np.tile(np.array([0, 1], np.int8), R)
+    d_rc = torch.zeros(n * ML, dtype=torch.uint8, device="cuda")
+    d_rl = torch.zeros(n, dtype=torch.int32, device="cuda")
+    prop.read_codes(dev(reads.seq), dev(reads.offsets), dev(idx), dev(st), n, ML, d_rc, d_rl)
+    d_er = torch.zeros(n * 128, dtype=torch.float32, device="cuda")
+    prop.embed(d_rc, d_rl, ML, n, ML, d_er)
+    torch.cuda.synchronize()
+    ef = po.bf16_round(d_ef.cpu().numpy().reshape(NF, 128))
+    er = po.bf16_round(d_er.cpu().numpy().reshape(R, 2, 128))
+    assert np.array_equal(ef[f1], ef[f2])
+    sc = np.maximum(er[:, 0, :] @ ef.T, er[:, 1, :] @ ef.T)      # [R][NF], fp64
+    Kc = min(K, NF)
+    tol = 1e-5
+    for i in range(R):
+        got = cand[i]
+        assert (got[Kc:] == -1).all()
+        got = got[:Kc]
+        assert len(set(got.tolist())) == Kc and (got >= 0).all() and (got < NF).all(), i
+        kth = np.sort(sc[i])[::-1][Kc - 1]
+        gs = sc[i][got]
+        assert (gs >= kth - tol).all(), (i, gs.min(), kth)
+        assert (np.diff(gs) <= tol).all(), i                       # score order
+        for a in range(Kc - 1):  # identical embeddings score identically: lower fragment first
+            if np.array_equal(ef[got[a]], ef[got[a + 1]]):
+                assert got[a] < got[a + 1], (i, a)
+        if f2 in got:
+            assert f1 in got and list(got).index(f1) < list(got).index(f2), i
+    prop.close()
+    g.close()
+
+
 def test_topk_consistent_with_oracle_scores(mss):
     import torch
     wl, genome, reads, g, prop = _proposal_setup(mss)
