@@ -61,7 +61,10 @@ def _lib():
             lib.orc_mss.restype = i64
             lib.orc_diag_score.argtypes = [P, i32, P, i64, i32, i32]
             lib.orc_diag_score.restype = i32
+            lib.orc_diag_score_step.argtypes = [P, i32, P, i64, i32, i32, i32]
+            lib.orc_diag_score_step.restype = i32
             lib.orc_map_read.argtypes = [P, i64, i64, P, i32, i32, i32, ctypes.POINTER(Hit), P]
+            lib.orc_map_read_step.argtypes = [P, i64, i64, P, i32, i32, i32, i32, ctypes.POINTER(Hit), P]
             lib.orc_revcomp.argtypes = [P, i32, P]
             lib.orc_revcomp.restype = None
             lib.orc_encode.argtypes = [P, i64, P]
@@ -70,6 +73,8 @@ def _lib():
             lib.orc_nw_literal.argtypes = [P, i64, i64, i32, P, i32, i32, i32, i32, i32, ctypes.POINTER(Aln),
                                            ctypes.c_char_p, i32]
             lib.orc_map_batch.argtypes = [P, i64, i64, P, P, i32, i32, i32, i32, i32, i32, i32, i32, P, P, P, i32]
+            lib.orc_map_batch_step.argtypes = [P, i64, i64, P, P, i32, i32, i32, i32, i32, i32, i32, i32, i32, P, P, P,
+                                               i32]
             _LIB = lib
     return _LIB
 
@@ -110,21 +115,28 @@ def mss(x) -> int:
     return int(_lib().orc_mss(_p(a), a.shape[0]))
 
 
-def diag_score(qcodes, gcodes_padded, d: int, match: int, mismatch: int) -> int:
+def diag_score(qcodes, gcodes_padded, d: int, match: int, mismatch: int, step: int = 1) -> int:
+    """step 2: the read sampled at every other position ("MaxSSmap_fast")."""
     q = np.ascontiguousarray(qcodes, dtype=np.uint8)
     g = np.ascontiguousarray(gcodes_padded, dtype=np.uint8)
     assert d + q.shape[0] <= g.shape[0]
-    return int(_lib().orc_diag_score(_p(q), q.shape[0], _p(g), d, match, mismatch))
+    if step == 1:
+        return int(_lib().orc_diag_score(_p(q), q.shape[0], _p(g), d, match, mismatch))
+    return int(_lib().orc_diag_score_step(_p(q), q.shape[0], _p(g), d, match, mismatch, step))
 
 
-def map_read(genome, F: int, read, match: int, mismatch: int, with_frag_scores: bool = False):
+def map_read(genome, F: int, read, match: int, mismatch: int, with_frag_scores: bool = False, step: int = 1):
     g = _buf(genome)
     r = _buf(read)
     h = Hit()
     NF = (g.shape[0] + F - 1) // F
     fs = np.empty(NF, dtype=np.int32) if with_frag_scores else None
-    rc = _lib().orc_map_read(_p(g), g.shape[0], F, _p(r), r.shape[0], match, mismatch, ctypes.byref(h),
-                             _p(fs) if fs is not None else None)
+    if step == 1:
+        rc = _lib().orc_map_read(_p(g), g.shape[0], F, _p(r), r.shape[0], match, mismatch, ctypes.byref(h),
+                                 _p(fs) if fs is not None else None)
+    else:
+        rc = _lib().orc_map_read_step(_p(g), g.shape[0], F, _p(r), r.shape[0], match, mismatch, step,
+                                      ctypes.byref(h), _p(fs) if fs is not None else None)
     if rc != 0:
         raise ValueError(f"orc_map_read failed ({rc})")
     return (h.as_tuple(), fs) if with_frag_scores else h.as_tuple()
@@ -162,7 +174,7 @@ ALN_DTYPE = np.dtype([("score", np.int32), ("cigar_len", np.int32), ("gstart", n
 
 
 def map_batch(genome, F: int, reads: np.ndarray, offsets: np.ndarray, match: int, mismatch: int,
-              nw=None, cigar_cap: int = 1024):
+              nw=None, cigar_cap: int = 1024, step: int = 1):
     """Phase one (and phase two when nw = (match, mismatch, open, extend, W)) for a batch.
     Returns (hits structured array, alns structured array or None, list of CIGAR strings or None)."""
     g = _buf(genome)
@@ -173,9 +185,9 @@ def map_batch(genome, F: int, reads: np.ndarray, offsets: np.ndarray, match: int
     alns = np.zeros(R, dtype=ALN_DTYPE) if nw is not None else None
     cig = np.zeros((R, cigar_cap), dtype=np.uint8) if nw is not None else None
     nm, nmm, go, ge, W = nw if nw is not None else (0, 0, 0, 0, 0)
-    rc = _lib().orc_map_batch(_p(g), g.shape[0], F, _p(rd), _p(off), R, match, mismatch, nm, nmm, go, ge, W,
-                              _p(hits), _p(alns) if alns is not None else None,
-                              _p(cig) if cig is not None else None, cigar_cap)
+    rc = _lib().orc_map_batch_step(_p(g), g.shape[0], F, _p(rd), _p(off), R, match, mismatch, step, nm, nmm, go,
+                                   ge, W, _p(hits), _p(alns) if alns is not None else None,
+                                   _p(cig) if cig is not None else None, cigar_cap)
     if rc != 0:
         raise ValueError(f"orc_map_batch failed ({rc})")
     cigars = None

@@ -50,29 +50,43 @@ int64_t orc_mss(const int32_t* x, int64_t n) {
   return best;
 }
 
-/* substitution scores of the read against the genome window that starts at diagonal d */
-static void diag_scores(const uint8_t* q, int32_t m, const uint8_t* g, int64_t d, int32_t match, int32_t mismatch,
-                        int32_t* x) {
-  for (int32_t k = 0; k < m; ++k) {
+/* substitution scores of the read against the genome window that starts at diagonal d, at
+   read positions 0, step, 2 step, ... (step 1: every base; step 2: "MaxSSmap_fast", every other
+   nucleotide of the read); returns how many scores were written */
+static int32_t diag_scores(const uint8_t* q, int32_t m, const uint8_t* g, int64_t d, int32_t match,
+                           int32_t mismatch, int32_t step, int32_t* x) {
+  int32_t n = 0;
+  for (int32_t k = 0; k < m; k += step) {
     uint8_t a = q[k], b = g[d + k];
-    x[k] = (a < 4 && a == b) ? match : mismatch;
+    x[n++] = (a < 4 && a == b) ? match : mismatch;
   }
+  return n;
 }
 
 /* One ungapped read-vs-genome diagonal ("First phase of MaxSSmap"): the substitution score
    sequence of the read against the genome window starting at d, then its maximum scoring
    subsequence. */
-int32_t orc_diag_score(const uint8_t* q, int32_t m, const uint8_t* g, int64_t d, int32_t match, int32_t mismatch) {
+int32_t orc_diag_score_step(const uint8_t* q, int32_t m, const uint8_t* g, int64_t d, int32_t match,
+                            int32_t mismatch, int32_t step) {
   int32_t* x = (int32_t*)malloc(sizeof(int32_t) * (size_t)(m > 0 ? m : 1));
-  diag_scores(q, m, g, d, match, mismatch, x);
-  int64_t v = orc_mss(x, m);
+  int32_t n = diag_scores(q, m, g, d, match, mismatch, step, x);
+  int64_t v = orc_mss(x, n);
   free(x);
   return (int32_t)v;
 }
 
+int32_t orc_diag_score(const uint8_t* q, int32_t m, const uint8_t* g, int64_t d, int32_t match, int32_t mismatch) {
+  return orc_diag_score_step(q, m, g, d, match, mismatch, 1);
+}
+
 int orc_map_read(const char* genome, int64_t G, int64_t F, const char* read, int32_t m, int32_t match,
                  int32_t mismatch, orc_hit* out, int32_t* frag_scores) {
-  if (G <= 0 || F <= 0 || m <= 0 || !out) return -1;
+  return orc_map_read_step(genome, G, F, read, m, match, mismatch, 1, out, frag_scores);
+}
+
+int orc_map_read_step(const char* genome, int64_t G, int64_t F, const char* read, int32_t m, int32_t match,
+                      int32_t mismatch, int32_t step, orc_hit* out, int32_t* frag_scores) {
+  if (G <= 0 || F <= 0 || m <= 0 || !out || (step != 1 && step != 2)) return -1;
   int64_t NF = (G + F - 1) / F;
   int64_t Gp = NF * F;
   /* genome codes, padded with N up to Gp + m - 1 ("Coalescent global memory access": the last
@@ -98,8 +112,8 @@ int orc_map_read(const char* genome, int64_t G, int64_t F, const char* read, int
      bases up to (f+1)F + m - 1 (the junction into the right neighbour) */
   for (int32_t sg = 0; sg < 2; ++sg) {
     for (int64_t d = 0; d < Gp; ++d) {
-      diag_scores(q[sg], m, g, d, match, mismatch, x);
-      int32_t K = (int32_t)orc_mss(x, m);
+      int32_t n = diag_scores(q[sg], m, g, d, match, mismatch, step, x);
+      int32_t K = (int32_t)orc_mss(x, n);
       int64_t f = d / F;
       if (K > S[f]) { /* strictly greater: + strand before -, then the smallest d */
         S[f] = K;
@@ -296,12 +310,20 @@ int orc_nw_literal(const uint8_t* gcodes, int64_t G, int64_t F, int32_t best_fra
 int orc_map_batch(const char* genome, int64_t G, int64_t F, const char* reads, const int64_t* offsets, int32_t R,
                   int32_t match, int32_t mismatch, int32_t nw_match, int32_t nw_mismatch, int32_t gap_open,
                   int32_t gap_extend, int32_t W, orc_hit* hits, orc_aln* alns, char* cigars, int32_t cigar_cap) {
+  return orc_map_batch_step(genome, G, F, reads, offsets, R, match, mismatch, 1, nw_match, nw_mismatch, gap_open,
+                            gap_extend, W, hits, alns, cigars, cigar_cap);
+}
+
+int orc_map_batch_step(const char* genome, int64_t G, int64_t F, const char* reads, const int64_t* offsets,
+                       int32_t R, int32_t match, int32_t mismatch, int32_t step, int32_t nw_match,
+                       int32_t nw_mismatch, int32_t gap_open, int32_t gap_extend, int32_t W, orc_hit* hits,
+                       orc_aln* alns, char* cigars, int32_t cigar_cap) {
   uint8_t* g = (uint8_t*)malloc((size_t)G);
   if (!g) return -2;
   if (orc_encode(genome, G, g) != 0) { free(g); return -1; }
   for (int32_t r = 0; r < R; ++r) {
     int32_t m = (int32_t)(offsets[r + 1] - offsets[r]);
-    int rc = orc_map_read(genome, G, F, reads + offsets[r], m, match, mismatch, &hits[r], 0);
+    int rc = orc_map_read_step(genome, G, F, reads + offsets[r], m, match, mismatch, step, &hits[r], 0);
     if (rc != 0) { free(g); return rc; }
     if (alns) {
       uint8_t* q = (uint8_t*)malloc((size_t)m);

@@ -52,6 +52,11 @@ int64_t orc_mss(const int32_t* x, int64_t n);
    codes g[d .. d+m) (codes 0..3 bases, 4 = N); s = match iff q[k]==g[d+k] and both < 4 */
 int32_t orc_diag_score(const uint8_t* q, int32_t m, const uint8_t* g, int64_t d, int32_t match, int32_t mismatch);
 
+/* the same with the read sampled at positions 0, step, 2 step, ... ("MaxSSmap_fast" considers
+   every other nucleotide of the read: step 2); step 1 is orc_diag_score */
+int32_t orc_diag_score_step(const uint8_t* q, int32_t m, const uint8_t* g, int64_t d, int32_t match,
+                            int32_t mismatch, int32_t step);
+
 typedef struct {
   int32_t best_frag;
   int32_t second_frag;
@@ -69,6 +74,11 @@ typedef struct {
  */
 int orc_map_read(const char* genome, int64_t G, int64_t F, const char* read, int32_t m, int32_t match,
                  int32_t mismatch, orc_hit* out, int32_t* frag_scores);
+
+/* phase one with the read sampled every step bases (1 or 2; 2 = "MaxSSmap_fast"), on both
+   strands (the reverse strand is sampled after reverse complementing) */
+int orc_map_read_step(const char* genome, int64_t G, int64_t F, const char* read, int32_t m, int32_t match,
+                      int32_t mismatch, int32_t step, orc_hit* out, int32_t* frag_scores);
 
 /* reverse complement of codes (4 stays 4) */
 void orc_revcomp(const uint8_t* q, int32_t m, uint8_t* out);
@@ -112,6 +122,10 @@ int orc_encode(const char* s, int64_t n, uint8_t* out);
 int orc_map_batch(const char* genome, int64_t G, int64_t F, const char* reads, const int64_t* offsets, int32_t R,
                   int32_t match, int32_t mismatch, int32_t nw_match, int32_t nw_mismatch, int32_t gap_open,
                   int32_t gap_extend, int32_t W, orc_hit* hits, orc_aln* alns, char* cigars, int32_t cigar_cap);
+int orc_map_batch_step(const char* genome, int64_t G, int64_t F, const char* reads, const int64_t* offsets,
+                       int32_t R, int32_t match, int32_t mismatch, int32_t step, int32_t nw_match,
+                       int32_t nw_mismatch, int32_t gap_open, int32_t gap_extend, int32_t W, orc_hit* hits,
+                       orc_aln* alns, char* cigars, int32_t cigar_cap);
 
 #ifdef __cplusplus
 }

@@ -52,8 +52,9 @@ def test_mss_special_cases():
 
 
 # ---------------------------------------------------------------- one diagonal, tiny inputs
-def brute_diag(read: str, gpad: str, d: int, match: int, mismatch: int) -> int:
-    x = [sub_score(read[k], gpad[d + k], match, mismatch) for k in range(len(read))]
+def brute_diag(read: str, gpad: str, d: int, match: int, mismatch: int, step: int = 1) -> int:
+    """step 2: only read positions 0, 2, 4, ... take part ("MaxSSmap_fast")."""
+    x = [sub_score(read[k], gpad[d + k], match, mismatch) for k in range(0, len(read), step)]
     return brute_mss(x)
 
 
@@ -73,7 +74,7 @@ def test_diag_score_bruteforce(match, mismatch):
 
 
 # ---------------------------------------------------------------- whole phase one, tiny inputs
-def brute_map(genome: str, F: int, read: str, match: int, mismatch: int):
+def brute_map(genome: str, F: int, read: str, match: int, mismatch: int, step: int = 1):
     """Phase one by enumeration: every strand, every diagonal of every fragment, every
     substring; fragment maximum with its first (strand, d); top two by sorting."""
     G = len(genome)
@@ -87,7 +88,7 @@ def brute_map(genome: str, F: int, read: str, match: int, mismatch: int):
         cands = []
         for sg in range(2):
             for d in range(f * F, (f + 1) * F):
-                cands.append((brute_diag(reads[sg], gpad, d, match, mismatch), sg, d))
+                cands.append((brute_diag(reads[sg], gpad, d, match, mismatch, step), sg, d))
         best = max(c[0] for c in cands)
         first = min((sg, d) for (s, sg, d) in cands if s == best)
         frag.append((best, first[0], first[1]))
@@ -119,6 +120,73 @@ def test_map_read_bruteforce(F):
         got, fs = oracle.map_read(genome, F, read, match, mismatch, with_frag_scores=True)
         assert got == want, (genome, F, read)
         assert fs.tolist() == wfs
+
+
+# ---------------------------------------------------------------- MaxSSmap_fast (read step 2)
+@pytest.mark.parametrize("match,mismatch", [(1, -1), (5, -4), (2, -7)])
+def test_fast_diag_score_bruteforce(match, mismatch):
+    """Every other read base: brute force over all runs of the sampled score sequence."""
+    rng = np.random.default_rng(40 + match)
+    for _ in range(60):
+        G = int(rng.integers(1, 40))
+        m = int(rng.integers(1, 13))
+        genome = "".join(rng.choice(list(ALPHA), p=[.22, .22, .22, .22, .12], size=G))
+        read = "".join(rng.choice(list(ALPHA), p=[.23, .23, .23, .23, .08], size=m))
+        gpad = genome + "N" * m
+        q, g = oracle.encode(read), oracle.encode(gpad)
+        for d in range(G):
+            assert oracle.diag_score(q, g, d, match, mismatch, step=2) == brute_diag(read, gpad, d, match, mismatch, 2)
+
+
+def test_fast_equals_plain_scan_of_subsampled_sequences():
+    """Sampling identity: diagonal d with step 2 is the plain diagonal d // 2 of the read's even
+    positions against the genome positions of d's parity."""
+    rng = np.random.default_rng(44)
+    for _ in range(40):
+        G = int(rng.integers(2, 60))
+        m = int(rng.integers(1, 15))
+        genome = "".join(rng.choice(list(ALPHA), p=[.23, .23, .23, .23, .08], size=G))
+        read = "".join(rng.choice(list(ALPHA), p=[.24, .24, .24, .24, .04], size=m))
+        gpad = genome + "N" * (m + 2)
+        q, g = oracle.encode(read), oracle.encode(gpad)
+        qs = oracle.encode(read[::2])
+        for d in range(G):
+            gs = oracle.encode(gpad[d % 2::2])
+            assert oracle.diag_score(q, g, d, 5, -4, step=2) == oracle.diag_score(qs, gs, d // 2, 5, -4)
+
+
+@pytest.mark.parametrize("F", [1, 4, 7, 16])
+def test_fast_map_read_bruteforce(F):
+    rng = np.random.default_rng(50 + F)
+    for trial in range(20):
+        G = int(rng.integers(1, 48))
+        m = int(rng.integers(1, 11))
+        genome = "".join(rng.choice(list(ALPHA), p=[.23, .23, .23, .23, .08], size=G))
+        if trial % 3 == 0 and G >= m:
+            s0 = int(rng.integers(0, G - m + 1))
+            read = genome[s0:s0 + m]
+            if trial % 2:
+                read = revcomp(read)
+        else:
+            read = "".join(rng.choice(list(ALPHA), p=[.24, .24, .24, .24, .04], size=m))
+        match, mismatch = [(1, -1), (5, -4), (2, -3)][trial % 3]
+        want, wfs = brute_map(genome, F, read, match, mismatch, step=2)
+        got, fs = oracle.map_read(genome, F, read, match, mismatch, with_frag_scores=True, step=2)
+        assert got == want, (genome, F, read)
+        assert fs.tolist() == wfs
+
+
+def test_fast_exact_substring_scores_half_length():
+    """An exact copy scores ceil(m / 2) * match at its diagonal with step 2."""
+    rng = np.random.default_rng(46)
+    genome = "".join(rng.choice(list("ACGT"), size=3000))
+    for m in (1, 2, 7, 50, 101):
+        s0 = 1234
+        read = genome[s0:s0 + m]
+        hit = oracle.map_read(genome, 500, read, 5, -4, step=2)
+        assert hit[2] == 5 * ((m + 1) // 2)
+        if m >= 50:  # long enough to be unique: found at its own diagonal, + strand
+            assert hit[4] == s0 and hit[5] == 0
 
 
 # ---------------------------------------------------------------- invariants
