@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-reads-per-core", type=int, default=2)
+    ap.add_argument("--read-step", type=int, default=1, choices=[1, 2],
+                    help="2: MaxSSmap_fast (every other read base in phase one)")
     return ap.parse_args()
 
 
@@ -70,16 +72,18 @@ def workload(args, rank: int):
     return wl, genome, seq, off
 
 
-def cells_of(lengths: np.ndarray, G: int, F: int) -> int:
+def cells_of(lengths: np.ndarray, G: int, F: int, step: int = 1) -> int:
+    """Scan cells: read positions taking part (every base, or every other one with read step 2)
+    x padded diagonals x 2 strands."""
     Gp = -(-G // F) * F
-    return int(lengths.astype(np.int64).sum()) * Gp * 2
+    return int(((lengths.astype(np.int64) + step - 1) // step).sum()) * Gp * 2
 
 
 # ------------------------------------------------------------------------------- CPU oracle
 def _oracle_job(args):
     import oracle
-    genome, F, seq, off, match, mismatch, nw = args
-    oracle.map_batch(genome, F, seq, off, match, mismatch, nw=nw)
+    genome, F, seq, off, match, mismatch, nw, step = args
+    oracle.map_batch(genome, F, seq, off, match, mismatch, nw=nw, step=step)
     return int(off.shape[0] - 1)
 
 
@@ -93,7 +97,7 @@ def cpu_sample(seq, off, n):
     return s, o
 
 
-def time_oracle(wl, genome, seq, off, cores, reads_per_core, pool):
+def time_oracle(wl, genome, seq, off, cores, reads_per_core, pool, step=1):
     n = max(1, cores * reads_per_core)
     s, o = cpu_sample(seq, off, n)
     bounds = np.linspace(0, n, cores + 1).astype(int)
@@ -102,11 +106,11 @@ def time_oracle(wl, genome, seq, off, cores, reads_per_core, pool):
         if b <= a:
             continue
         jobs.append((genome, wl.frag_len, np.ascontiguousarray(s[o[a]:o[b]]),
-                     np.ascontiguousarray(o[a:b + 1] - o[a]), wl.match, wl.mismatch, wl.nw))
+                     np.ascontiguousarray(o[a:b + 1] - o[a]), wl.match, wl.mismatch, wl.nw, step))
     t0 = time.perf_counter()
     done = sum(pool.map(_oracle_job, jobs))
     dt = time.perf_counter() - t0
-    cells = cells_of(np.diff(o), genome.shape[0], wl.frag_len)
+    cells = cells_of(np.diff(o), genome.shape[0], wl.frag_len, step)
     return cells, done, dt
 
 
@@ -125,11 +129,11 @@ def run_reference(args):
     cores = host_cores()
     with ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn")) as pool:
         for _ in range(args.warmup):
-            time_oracle(wl, genome, seq, off, cores, 1, pool)
+            time_oracle(wl, genome, seq, off, cores, 1, pool, args.read_step)
         tot_cells = tot_reads = 0
         tot_t = 0.0
         for _ in range(args.steps):
-            c, r, dt = time_oracle(wl, genome, seq, off, cores, 1, pool)
+            c, r, dt = time_oracle(wl, genome, seq, off, cores, 1, pool, args.read_step)
             tot_cells += c
             tot_reads += r
             tot_t += dt
@@ -140,7 +144,8 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": round(gcups, 4), "unit": "GCUPS", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(tot_t / args.steps * 1e3, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": wl.name, "genome_bp": int(genome.shape[0]), "frag_len": wl.frag_len},
+        "config": {"workload": wl.name, "genome_bp": int(genome.shape[0]), "frag_len": wl.frag_len,
+                   "read_step": args.read_step},
         "reads_per_s": round(tot_reads / tot_t, 3),
         "cpu_baseline": {"value": round(gcups, 4), "unit": "GCUPS", "cores": cores, "kind": "oracle",
                          "sample": sample},
@@ -224,14 +229,14 @@ def main():
     R = int(lengths.shape[0])
     max_len = int(lengths.max())
     nm, nmm, go, ge, W = wl.nw
-    cells_step = cells_of(lengths, genome.shape[0], wl.frag_len)
+    cells_step = cells_of(lengths, genome.shape[0], wl.frag_len, args.read_step)
 
     # CPU baseline first (rank 0, N = 1), before the GPU is busy
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cores = host_cores()
         with ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn")) as pool:
-            c, r, dt = time_oracle(wl, genome, seq, off, cores, args.cpu_reads_per_core, pool)
+            c, r, dt = time_oracle(wl, genome, seq, off, cores, args.cpu_reads_per_core, pool, args.read_step)
         cpu = {"value": round(c / dt / 1e9, 4), "unit": "GCUPS", "cores": cores, "kind": "oracle",
                "sample": f"{r} reads ({args.cpu_reads_per_core} per core, evenly spaced over the workload), "
                          f"phase one + banded NW, {dt:.1f} s wall on {cores} processes",
@@ -242,6 +247,7 @@ def main():
     props = torch.cuda.get_device_properties(dev)
     g = mss.mss_load_genome(genome, frag_len=wl.frag_len, max_read_len=max_len)
     info = g.info()
+    mss.mss_set_read_step(g, args.read_step)
     mss.mss_scan_timing(g, True)
     stream = torch.cuda.Stream(device=dev)
     d_seq = torch.from_numpy(seq).to(dev)
@@ -261,6 +267,7 @@ def main():
         for i in range(args.warmup):
             step()
         mss.mss_sync(g, stream=stream)
+        probe = mss.mss_probe_pipes()[0] if rank == 0 else None   # pipe rates, outside the timed region
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(args.steps)]
         scan_ms = []
@@ -322,6 +329,9 @@ def main():
     if rank == 0:
         sms = props.multi_processor_count
         peak = peak_tcups(sms, 2070.0)
+        # the integer/DPX pipe alone, measured by the library's pipe probe: warp-instructions per
+        # SM clock x 32 threads x 2 lanes / 2 ops per cell, at the same clock
+        dpx_only = probe[0] * 32 * sms * 2070.0e6 / 1e12 if probe else None
         scan_mean_ms = statistics.mean(scan_ms)
         achieved = cells_step / (scan_mean_ms * 1e-3) / 1e12
         tune = mss.mss_get_tune(g)
@@ -333,7 +343,8 @@ def main():
                        "padded_bp": info["padded_len"], "reads": R, "read_lengths": sorted(set(lengths.tolist())),
                        "scores": [wl.match, wl.mismatch], "nw": list(wl.nw),
                        "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
-                       "parallelism": f"replicas x{world} (read batches per GPU)", "scan_tune": tune},
+                       "parallelism": f"replicas x{world} (read batches per GPU)", "scan_tune": tune,
+                       "read_step": args.read_step},
             "reads_per_s": round(reads_s, 1),
             "e2e": e2e,
             "gpu_launches": int(launches),
@@ -342,7 +353,9 @@ def main():
                          "frac": round(achieved / peak, 4), "traffic": None,
                          "peak_source": f"derived: {sms} SMs x 4 sub-partitions x 32 cells/clk (16-lane integer/DPX "
                                         "pipe + 16-lane FMA pipe, packed 16-bit x2, 2 ops per cell) x 2070 MHz",
-                         "scan_ms_per_step": round(scan_mean_ms, 3)},
+                         "scan_ms_per_step": round(scan_mean_ms, 3),
+                         "peak_dpx_pipe_only": round(dpx_only, 3) if dpx_only else None,
+                         "frac_of_dpx_pipe_only": round(achieved / dpx_only, 4) if dpx_only else None},
             "cpu_baseline": cpu,
             "clocks": clk,
         }

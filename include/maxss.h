@@ -135,6 +135,16 @@ MSS_API mss_status mss_load_genome_device(mss_ctx** out, const char* d_seq, int6
 MSS_API mss_status mss_get_info(const mss_ctx* ctx, mss_genome_info* info);
 /* Change F after loading (the packed genome does not depend on F). */
 MSS_API mss_status mss_set_frag_len(mss_ctx* ctx, int64_t frag_len);
+/* Read step of phase one ("MaxSSmap_fast" paragraph: the faster version considers every other
+   nucleotide of the read): 1 = every read base (default), 2 = read bases 0, 2, 4, ... only,
+   i.e. step k of diagonal d compares read base 2k with genome base d + 2k, on each strand
+   after reverse complementing.  Fragment maxima, top-2, the repeat flag and the best
+   diagonal follow from those scores; phase two (nw_align) always aligns the whole read.
+   Step 2 runs with the default scan shape (8 lane pairs x 4 query strands); other mss_tune
+   shapes make the mapping calls fail with MSS_EINVAL.  Errors: MSS_EINVAL for a null ctx or
+   a step other than 1 or 2. */
+MSS_API mss_status mss_set_read_step(mss_ctx* ctx, int32_t step);
+MSS_API int32_t mss_get_read_step(const mss_ctx* ctx);  /* -1 for a null ctx */
 MSS_API mss_status mss_set_tune(mss_ctx* ctx, const mss_tune* t);
 MSS_API mss_status mss_get_tune(const mss_ctx* ctx, mss_tune* t);
 
@@ -284,6 +294,30 @@ MSS_API mss_status mss_map_reads_proposed(mss_ctx* ctx, mss_prop* p, const char*
 MSS_API mss_status mss_prop_save(const mss_prop* p, const char* path);
 MSS_API mss_status mss_prop_load(mss_prop* p, const char* path);
 MSS_API int64_t mss_prop_launch_count(const mss_prop* p);
+
+/* ---- SAM output ("Mapping qualities, read lengths, SAM output, and source code") ---- */
+/* MAPQ of a phase-one result: -100 log2(second / best), the paper's probability of a wrong
+   mapping being the ratio of the second-best to the best fragment score; rounded to the
+   nearest integer, capped at 254; 254 when second_score == 0; 0 when best_score <= 0 or
+   second_score >= best_score.  A read counts as mapped when MAPQ > 15.2, i.e. when the
+   MSS_HIT_REPEAT flag is clear.  Pure function of its arguments. */
+MSS_API int32_t mss_mapq(int32_t best_score, int32_t second_score);
+/* SAM text (host memory only) for R reads: optional header (@HD, @SQ SN:ref_name LN:ref_len,
+   @PG), then one line per read: QNAME r<index>, FLAG 0 / 16 (reverse strand) / 4 (unmapped:
+   repeat-flagged in phase one or no in-band alignment in phase two), RNAME, POS =
+   alns[r].gstart + 1, MAPQ (mss_mapq), CIGAR from cigars + r * cigar_stride (alns[r].cigar_len
+   characters; '*' when cigars is NULL or the slot overflowed), RNEXT '*', PNEXT 0, TLEN 0,
+   SEQ on the forward genome strand (reverse complement for strand 1, upper case), QUAL '*',
+   tags AS:i (phase-two score, mapped reads), ZM:i (best fragment score), XS:i (second
+   fragment score).  reads/offsets: the concatenated reads (offsets[R + 1]); hits/alns: the
+   results of mss_map_reads / nw_align.  Returns the text length in bytes (without the NUL);
+   the text and a NUL are written to out only when out != NULL and cap > length, so a call
+   with out == NULL sizes the buffer.  Negative MSS_EINVAL for a null or empty ref_name (or
+   one holding tabs, spaces or newlines), ref_len < 1, R < 0, missing arrays, a negative read
+   length, or cigar_stride < 1 with cigars given.  Touches no GPU. */
+MSS_API int64_t mss_format_sam(const char* ref_name, int64_t ref_len, const char* reads, const int64_t* offsets,
+                               int32_t R, const mss_hit* hits, const mss_aln* alns, const char* cigars,
+                               int32_t cigar_stride, int32_t header, char* out, int64_t cap);
 
 MSS_API void mss_free(mss_ctx* ctx);
 MSS_API const char* mss_last_error(void);

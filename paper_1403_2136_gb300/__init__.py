@@ -28,13 +28,14 @@ MSS_NW_NONE = -2147483648
 MSS_HIT_REPEAT = 1
 
 # every symbol include/maxss.h declares
-EXPORTS = ("mss_load_genome", "mss_load_genome_device", "mss_get_info", "mss_set_frag_len", "mss_set_tune",
+EXPORTS = ("mss_load_genome", "mss_load_genome_device", "mss_get_info", "mss_set_frag_len", "mss_set_read_step",
+           "mss_get_read_step", "mss_set_tune",
            "mss_get_tune", "mss_map_reads", "mss_map_reads_device", "nw_align", "nw_align_device", "nw_align_device_noalloc", "mss_map_align", "mss_sync",
            "mss_autotune", "mss_scan_timing", "mss_scan_time_ms", "mss_launch_count", "mss_genome_codes", "mss_probe_pipes", "mss_prop_create", "mss_prop_free", "mss_prop_param_count",
            "mss_prop_get_params", "mss_prop_set_params", "mss_prop_read_codes", "mss_prop_window_codes",
            "mss_prop_embed_device", "mss_prop_grad_device", "mss_prop_train_step", "mss_prop_build_index",
            "mss_map_reads_proposed", "mss_prop_save", "mss_prop_load", "mss_prop_launch_count", "mss_free",
-           "mss_last_error")
+           "mss_mapq", "mss_format_sam", "mss_last_error")
 
 HIT_DTYPE = np.dtype([("best_frag", np.int32), ("second_frag", np.int32), ("best_score", np.int32),
                       ("second_score", np.int32), ("offset", np.int64), ("strand", np.int32), ("flags", np.int32)])
@@ -89,6 +90,8 @@ def load_library(path: str = LIB_PATH):
         "mss_load_genome_device": ([ctypes.POINTER(P), P, i64, ctypes.POINTER(GenomeParams), P], i32),
         "mss_get_info": ([P, ctypes.POINTER(GenomeInfo)], i32),
         "mss_set_frag_len": ([P, i64], i32),
+        "mss_set_read_step": ([P, i32], i32),
+        "mss_get_read_step": ([P], i32),
         "mss_set_tune": ([P, ctypes.POINTER(Tune)], i32),
         "mss_get_tune": ([P, ctypes.POINTER(Tune)], i32),
         "mss_map_reads": ([P, P, P, i32, ctypes.POINTER(ScoreParams), P, P], i32),
@@ -124,6 +127,8 @@ def load_library(path: str = LIB_PATH):
         "mss_prop_launch_count": ([P], i64),
         "mss_free": ([P], None),
         "mss_last_error": ([], ctypes.c_char_p),
+        "mss_mapq": ([i32, i32], i32),
+        "mss_format_sam": ([ctypes.c_char_p, i64, P, P, i32, P, P, P, i32, i32, P, i64], i64),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -205,6 +210,15 @@ def mss_set_frag_len(g: Genome, frag_len: int):
     _check(load_library().mss_set_frag_len(g.handle, frag_len), "mss_set_frag_len")
 
 
+def mss_set_read_step(g: Genome, step: int):
+    """1: every read base; 2: every other read base ("MaxSSmap_fast")."""
+    _check(load_library().mss_set_read_step(g.handle, step), "mss_set_read_step")
+
+
+def mss_get_read_step(g: Genome) -> int:
+    return int(load_library().mss_get_read_step(g.handle))
+
+
 def mss_set_tune(g: Genome, variant=-1, pairs=0, queries=0, ctas_per_sm=0, min_items_per_cta=0):
     t = Tune(variant, pairs, queries, ctas_per_sm, min_items_per_cta, 0)
     _check(load_library().mss_set_tune(g.handle, ctypes.byref(t)), "mss_set_tune")
@@ -256,6 +270,35 @@ def nw_align(g: Genome, reads, offsets, hits: np.ndarray, match=5, mismatch=-4, 
     _check(st, "nw_align")
     cigars = [bytes(cig[i, :max(out["cigar_len"][i], 0)]).decode() for i in range(R)]
     return out, cigars
+
+
+def mss_mapq(best_score: int, second_score: int) -> int:
+    """-100 log2(second / best), rounded, capped at 254 ("Mapping qualities ..." paragraph)."""
+    return int(load_library().mss_mapq(int(best_score), int(second_score)))
+
+
+def format_sam(ref_name: str, genome_len: int, reads, offsets, hits, alns, cigars=None, header: bool = True) -> str:
+    """SAM text of mapped reads (host arrays; cigars: list of CIGAR strings from nw_align)."""
+    lib = load_library()
+    reads = np.ascontiguousarray(reads, dtype=np.uint8)
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    hits = np.ascontiguousarray(hits, dtype=HIT_DTYPE)
+    alns = np.ascontiguousarray(alns, dtype=ALN_DTYPE)
+    R = offsets.shape[0] - 1
+    cbuf, stride = None, 0
+    if cigars is not None:
+        stride = max([len(c) for c in cigars] + [0]) + 1
+        cbuf = np.zeros((max(R, 1), stride), dtype=np.uint8)
+        for i, c in enumerate(cigars):
+            cbuf[i, :len(c)] = np.frombuffer(c.encode(), dtype=np.uint8)
+    args = (ref_name.encode(), int(genome_len), _host_ptr(reads), _host_ptr(offsets), R, _host_ptr(hits),
+            _host_ptr(alns), _host_ptr(cbuf) if cbuf is not None else None, stride, 1 if header else 0)
+    n = lib.mss_format_sam(*args, None, 0)
+    if n < 0:
+        raise MssError(int(n), "mss_format_sam", "invalid arguments")
+    buf = ctypes.create_string_buffer(int(n) + 1)
+    lib.mss_format_sam(*args, buf, n + 1)
+    return buf.value.decode()
 
 
 def nw_align_device(g: Genome, d_reads, d_offsets, R: int, max_len: int, d_hits, d_out, d_cigars,

@@ -89,6 +89,7 @@ struct mss_ctx {
   int32_t* d_err = nullptr;
   int64_t launches = 0;
   mss_tune tune{-1, 0, 0, 0, 0, 0};  // automatic
+  int32_t read_step = 1;              // 2: "MaxSSmap_fast" (every other read base)
   DevBuf hist, order, partial, queue, nw_scratch;
   DevBuf h_reads, h_offsets, h_hits, h_alns, h_cigars;  // staging for the host-pointer calls
   cudaGraphExec_t graph = nullptr;
@@ -180,6 +181,9 @@ mss_status resolve_config(const mss_ctx* c, int32_t max_len, const mss_score_par
   cfg->queries = t.queries ? t.queries : (cfg->pairs == 8 ? 4 : 8);
   cfg->threads = 256;
   cfg->max_len = max_len;
+  cfg->step = c->read_step;
+  if (cfg->step == 2 && (cfg->pairs != 8 || cfg->queries != 4))
+    return fail(MSS_EINVAL, "read step 2 is built for 8 lane pairs x 4 query strands only");
   *slots = scan_ring_slots(*cfg, c->F);
   *smem = scan_smem_bytes(*cfg, max_len, *slots);
   if (*smem == 0)
@@ -267,6 +271,7 @@ mss_status enqueue_map(mss_ctx* c, const char* d_reads, const int64_t* d_offsets
   f.partial = (const int4*)c->partial.p;
   f.match = sp->match;
   f.mismatch = sp->mismatch;
+  f.step = cfg.step;
   f.hits = d_out;
   f.err = c->d_err;
   CK(launch_finalize(f, s), "finalize kernel");
@@ -515,6 +520,15 @@ mss_status mss_set_frag_len(mss_ctx* c, int64_t F) {
   c->set_frag(F);
   return MSS_OK;
 }
+
+mss_status mss_set_read_step(mss_ctx* c, int32_t step) {
+  if (check_ctx(c)) return MSS_EINVAL;
+  if (step != 1 && step != 2) return fail(MSS_EINVAL, "read step %d: 1 (every base) or 2 (every other base)", step);
+  c->read_step = step;
+  return MSS_OK;
+}
+
+int32_t mss_get_read_step(const mss_ctx* c) { return c ? c->read_step : -1; }
 
 mss_status mss_set_tune(mss_ctx* c, const mss_tune* t) {
   if (check_ctx(c) || !t) return fail(MSS_EINVAL, "null argument");

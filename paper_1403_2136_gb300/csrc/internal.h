@@ -40,6 +40,7 @@ struct ScanConfig {
   int queries;  // RQ
   int threads;  // NT
   int max_len;  // longest read of the call (selects the selector-row size)
+  int step;     // read step: 1 every base, 2 every other base ("MaxSSmap_fast")
 };
 
 struct ScanArgs {
@@ -71,6 +72,7 @@ size_t scan_smem_bytes(const ScanConfig& c, int32_t max_len, int32_t ring_slots)
 int scan_ring_slots(const ScanConfig& c, int64_t F);
 cudaError_t scan_max_ctas_per_sm(const ScanConfig& c, size_t smem, int* out);
 cudaError_t launch_scan(const ScanConfig& c, const ScanArgs& a, int grid, size_t smem, cudaStream_t s);
+bool scan_supported(const ScanConfig& c);
 
 struct FinalArgs {
   const uint32_t* g2;
@@ -85,6 +87,7 @@ struct FinalArgs {
   int32_t reads_per_group;
   const int4* partial;
   int32_t match, mismatch;
+  int32_t step;  // read step of the scan (the rescan samples the read the same way)
   void* hits;  // mss_hit[R], input order
   int32_t* err;
 };

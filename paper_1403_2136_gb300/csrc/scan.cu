@@ -68,15 +68,19 @@ __host__ __device__ inline SmemLayout scan_layout(int32_t max_len, int32_t ring_
   return L;
 }
 
-template <bool F16, int D, int RQ, int NT, int MAXL, int MINB>
+// STEP = 1: every read base; STEP = 2: every other read base ("MaxSSmap_fast"), so step k of
+// diagonal d compares read base STEP*k with genome base d + STEP*k.
+template <bool F16, int D, int RQ, int NT, int MAXL, int MINB, int STEP>
 __global__ void __launch_bounds__(NT, MINB) k_scan(ScanArgs a) {
   using Geo = ScanGeo<D, NT, MAXL>;
   constexpr int RG = RQ / 2;
   constexpr int SPAN = Geo::kSpan;
   constexpr int TILE = Geo::kTile;
   constexpr int W = Geo::kSelCols;
+  constexpr int BS = D / STEP;  // steps per block: a block consumes D genome positions
   static_assert(RQ % 4 == 0, "profile rows are read as uint4");
-  static_assert(D % 2 == 0, "the running max is updated every second step");
+  static_assert(STEP == 1 || STEP == 2, "read step 1 or 2");
+  static_assert(BS % 2 == 0, "the running max is updated every second step");
   static_assert(RG <= 4, "read lengths occupy 16 bytes of the misc area");
 
   extern __shared__ __align__(128) uint8_t smem[];
@@ -134,15 +138,18 @@ __global__ void __launch_bounds__(NT, MINB) k_scan(ScanArgs a) {
     int32_t mmax = 0;
 #pragma unroll
     for (int r = 0; r < RG; ++r) mmax = max(mmax, s_len[r]);
-    const int mpad = max(D, (mmax + D - 1) / D * D);
+    const int nsteps = (mmax + STEP - 1) / STEP;
+    const int mpad = max(BS, (nsteps + BS - 1) / BS * BS);
 
-    // query profile: prof[k * RQ + q], q = 2r (forward) or 2r + 1 (reverse complement)
+    // query profile: prof[k * RQ + q] for step k (read base STEP*k), q = 2r (forward) or 2r + 1
+    // (reverse complement)
     for (int e = tid; e < mpad * RQ; e += NT) {
       const int k = e / RQ, q = e - k * RQ, r = q >> 1;
       const int len = s_len[r];
+      const int kr = STEP * k;
       uint32_t code = 4;
-      if (k < len) {
-        const int64_t pos = s_off[r] + ((q & 1) ? (len - 1 - k) : k);
+      if (kr < len) {
+        const int64_t pos = s_off[r] + ((q & 1) ? (len - 1 - kr) : kr);
         code = ascii_code((uint8_t)a.reads[pos]);
         if (code == 5) {
           atomicOr(a.err, ERR_BAD_CHAR);
@@ -211,7 +218,7 @@ __global__ void __launch_bounds__(NT, MINB) k_scan(ScanArgs a) {
         const uint32_t* rgm = reinterpret_cast<const uint32_t*>(raw + buf * Geo::kRawBytes + Geo::kRawG2Bytes);
         // one selector column per thread: positions P .. P + SPAN - 1 and their partners at
         // +D; their 2-bit codes and valid bits fit in two aligned words each
-        const int ncols = (TILE + mpad + D + SPAN - 1) / SPAN;
+        const int ncols = (TILE + STEP * mpad + D + SPAN - 1) / SPAN;
         for (int col = tid; col < ncols; col += NT) {
           const int P = col * SPAN;
           const uint64_t gw = ((((uint64_t)rg2[(P >> 4) + 1]) << 32) | rg2[P >> 4]) >> (2 * (P & 15));
@@ -254,14 +261,16 @@ __global__ void __launch_bounds__(NT, MINB) k_scan(ScanArgs a) {
 #pragma unroll
       for (int v = 0; v < RQ / 4; ++v) pnext[v] = reinterpret_cast<const uint4*>(prof)[v];
 
-      for (int k0 = 0; k0 < mpad; k0 += D) {
-        // positions entering the window during this block: p = tid*SPAN + k0 + u + D, u < D,
-        // all in one selector row band and one column
-        const int kk = k0 + D;
+      for (int k0 = 0; k0 < mpad; k0 += BS) {
+        // positions entering the window during this block: p = tid*SPAN + STEP*k0 + D + i,
+        // i < D, all in one selector row band and one column; pair j of step k = k0 + u reads
+        // position tid*SPAN + STEP*k + j, kept in win[(j + STEP*u) % D] (STEP*k0 is a
+        // multiple of D)
+        const int kk = STEP * k0 + D;
         const uint32_t* sp = sel + (kk % SPAN) * W + tid + kk / SPAN;
         const uint4* pp = reinterpret_cast<const uint4*>(prof + (k0 + 1) * RQ);
 #pragma unroll
-        for (int u = 0; u < D; ++u) {
+        for (int u = 0; u < BS; ++u) {
           uint32_t pw[RQ];
 #pragma unroll
           for (int v = 0; v < RQ / 4; ++v) {
@@ -276,16 +285,17 @@ __global__ void __launch_bounds__(NT, MINB) k_scan(ScanArgs a) {
           for (int q = 0; q < RQ; ++q) {
 #pragma unroll
             for (int j = 0; j < D; ++j) {
-              const uint32_t s = prmt(pw[q], mmw, win[(j + u) % D]);
+              const uint32_t s = prmt(pw[q], mmw, win[(j + STEP * u) % D]);
               const uint32_t h = kadane_step<F16>(H[q][j], s);
               if ((u & 1) != (j & 1)) M[q][j] = __vimax3_s16x2(M[q][j], H[q][j], h);
               H[q][j] = h;
             }
           }
-          win[u] = sp[u * W];
+#pragma unroll
+          for (int e = 0; e < STEP; ++e) win[(STEP * u + e) % D] = sp[(STEP * u + e) * W];
         }
       }
-      // mpad is a multiple of D (even): the last step is odd, so pairs with odd j hold one
+      // mpad is a multiple of BS (even): the last step is odd, so pairs with odd j hold one
       // value not yet folded
 #pragma unroll
       for (int q = 0; q < RQ; ++q)
@@ -354,44 +364,51 @@ __global__ void __launch_bounds__(NT, MINB) k_scan(ScanArgs a) {
 }
 
 // ---------------------------------------------------------------- host side of the scan
-// (f16, D, RQ, NT, MAXL, min CTAs per SM)
-#define MSS_SCAN_VARIANTS(X)     \
-  X(false, 4, 8, 256, 512, 2)    \
-  X(true, 4, 8, 256, 512, 2)     \
-  X(false, 8, 4, 256, 512, 2)    \
-  X(true, 8, 4, 256, 512, 2)     \
-  X(false, 4, 4, 256, 512, 2)    \
-  X(true, 4, 4, 256, 512, 2)     \
-  X(false, 4, 8, 256, 2432, 2)   \
-  X(true, 4, 8, 256, 2432, 2)    \
-  X(false, 8, 4, 256, 2432, 2)   \
-  X(true, 8, 4, 256, 2432, 2)    \
-  X(false, 4, 4, 256, 2432, 2)   \
-  X(true, 4, 4, 256, 2432, 2)
+// (f16, D, RQ, NT, MAXL, min CTAs per SM, read step)
+#define MSS_SCAN_VARIANTS(X)        \
+  X(false, 4, 8, 256, 512, 2, 1)    \
+  X(true, 4, 8, 256, 512, 2, 1)     \
+  X(false, 8, 4, 256, 512, 2, 1)    \
+  X(true, 8, 4, 256, 512, 2, 1)     \
+  X(false, 4, 4, 256, 512, 2, 1)    \
+  X(true, 4, 4, 256, 512, 2, 1)     \
+  X(false, 4, 8, 256, 2432, 2, 1)   \
+  X(true, 4, 8, 256, 2432, 2, 1)    \
+  X(false, 8, 4, 256, 2432, 2, 1)   \
+  X(true, 8, 4, 256, 2432, 2, 1)    \
+  X(false, 4, 4, 256, 2432, 2, 1)   \
+  X(true, 4, 4, 256, 2432, 2, 1)    \
+  X(false, 8, 4, 256, 512, 2, 2)    \
+  X(true, 8, 4, 256, 512, 2, 2)     \
+  X(false, 8, 4, 256, 2432, 2, 2)   \
+  X(true, 8, 4, 256, 2432, 2, 2)
 
 // reads up to 512 bases use selector rows sized for 512 (less shared memory per CTA)
 static int maxl_of(int32_t max_len) { return max_len <= 512 ? 512 : 2432; }
 
-template <bool F16, int D, int RQ, int NT, int MAXL, int MINB>
+template <bool F16, int D, int RQ, int NT, int MAXL, int MINB, int STEP>
 static const void* scan_fn() {
-  return reinterpret_cast<const void*>(&k_scan<F16, D, RQ, NT, MAXL, MINB>);
+  return reinterpret_cast<const void*>(&k_scan<F16, D, RQ, NT, MAXL, MINB, STEP>);
 }
 
 static const void* pick_scan(const ScanConfig& c) {
   const int ml = maxl_of(c.max_len);
-#define X(f, d, rq, nt, mx, mb)                                                                   \
-  if (c.variant == (f ? 1 : 0) && c.pairs == d && c.queries == rq && c.threads == nt && ml == mx) \
-    return scan_fn<f, d, rq, nt, mx, mb>();
+#define X(f, d, rq, nt, mx, mb, st)                                                                \
+  if (c.variant == (f ? 1 : 0) && c.pairs == d && c.queries == rq && c.threads == nt && ml == mx && \
+      c.step == st)                                                                                \
+    return scan_fn<f, d, rq, nt, mx, mb, st>();
   MSS_SCAN_VARIANTS(X)
 #undef X
   return nullptr;
 }
 
+bool scan_supported(const ScanConfig& c) { return pick_scan(c) != nullptr; }
+
 int64_t scan_tile_diags(const ScanConfig& c) { return (int64_t)c.threads * 2 * c.pairs; }
 
 size_t scan_smem_bytes(const ScanConfig& c, int32_t max_len, int32_t ring_slots) {
   const int ml = maxl_of(max_len);
-#define X(f, d, rq, nt, mx, mb)                                                    \
+#define X(f, d, rq, nt, mx, mb, st)                                                \
   if (c.pairs == d && c.queries == rq && c.threads == nt && ml == mx)              \
     return scan_layout<d, rq, nt, mx>(max_len, ring_slots).total;
   MSS_SCAN_VARIANTS(X)
@@ -469,7 +486,7 @@ __global__ void __launch_bounds__(kFinWarps * 32) k_finalize(FinalArgs a) {
       __syncwarp();
       for (int64_t i = lane; i < nd; i += 32) {
         int32_t h = 0, mx = 0;
-        for (int k = 0; k < m; ++k) {
+        for (int k = 0; k < m; k += a.step) {
           const uint32_t qc = s_q[wib][sg][k], gc = s_gen[wib][i + k];
           h += (qc < 4 && qc == gc) ? a.match : a.mismatch;
           h = max(h, 0);

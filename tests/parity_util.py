@@ -15,25 +15,25 @@ ALN_FIELDS = ("score", "cigar_len", "gstart", "gend")
 
 
 def _oracle_chunk(args):
-    genome, F, seq, offsets, match, mismatch, nw = args
-    hits, alns, cig = oracle.map_batch(genome, F, seq, offsets, match, mismatch, nw=nw)
+    genome, F, seq, offsets, match, mismatch, nw, step = args
+    hits, alns, cig = oracle.map_batch(genome, F, seq, offsets, match, mismatch, nw=nw, step=step)
     return hits, alns, cig
 
 
-def oracle_map(genome, F, reads_seq, reads_off, match, mismatch, nw=None, procs: int | None = None):
+def oracle_map(genome, F, reads_seq, reads_off, match, mismatch, nw=None, procs: int | None = None, step: int = 1):
     """Run the oracle over reads; with procs > 1 the reads are split over a spawn pool."""
     R = reads_off.shape[0] - 1
     if procs is None:
         procs = 1
     if procs <= 1 or R <= 1:
-        return oracle.map_batch(genome, F, reads_seq, reads_off, match, mismatch, nw=nw)
+        return oracle.map_batch(genome, F, reads_seq, reads_off, match, mismatch, nw=nw, step=step)
     procs = min(procs, R)
     bounds = np.linspace(0, R, procs + 1).astype(int)
     jobs = []
     for a, b in zip(bounds[:-1], bounds[1:]):
         off = reads_off[a:b + 1] - reads_off[a]
         seq = reads_seq[reads_off[a]:reads_off[b]]
-        jobs.append((genome, F, np.ascontiguousarray(seq), np.ascontiguousarray(off), match, mismatch, nw))
+        jobs.append((genome, F, np.ascontiguousarray(seq), np.ascontiguousarray(off), match, mismatch, nw, step))
     with ProcessPoolExecutor(max_workers=procs, mp_context=mp.get_context("spawn")) as ex:
         parts = list(ex.map(_oracle_chunk, jobs))
     hits = np.concatenate([p[0] for p in parts])

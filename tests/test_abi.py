@@ -13,7 +13,7 @@ HEADER = os.path.join(ROOT, "include", "maxss.h")
 def declared_functions():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    names = re.findall(r"^\s*(?:MSS_API\s+)?(?:mss_status|void|int64_t|const char\*)\s+(\w+)\s*\(", text, flags=re.M)
+    names = re.findall(r"^\s*(?:MSS_API\s+)?(?:mss_status|void|int64_t|int32_t|const char\*)\s+(\w+)\s*\(", text, flags=re.M)
     return sorted(set(names))
 
 

@@ -24,15 +24,17 @@ def mss():
     return m
 
 
-def run_both(mss, genome, seq, off, F, match, mismatch, nw=None, max_len=None, tune=None, procs=None):
+def run_both(mss, genome, seq, off, F, match, mismatch, nw=None, max_len=None, tune=None, procs=None, step=1):
     g = mss.mss_load_genome(genome, frag_len=F, max_read_len=max_len or max(1, int(np.diff(off).max())))
     if tune:
         mss.mss_set_tune(g, **tune)
+    if step != 1:
+        mss.mss_set_read_step(g, step)
     hits = mss.mss_map_reads(g, seq, off, match, mismatch)
     alns = cig = None
     if nw is not None:
         alns, cig = mss.nw_align(g, seq, off, hits, *nw)
-    ohits, oalns, ocig = oracle_map(genome, F, seq, off, match, mismatch, nw=nw, procs=procs)
+    ohits, oalns, ocig = oracle_map(genome, F, seq, off, match, mismatch, nw=nw, procs=procs, step=step)
     g.close()
     return hits, alns, cig, ohits, oalns, ocig
 
@@ -222,3 +224,65 @@ def test_genome_sharding_on_gpu_equals_unsharded(mss, world):
     want = mss.mss_map_reads(g, reads.seq, reads.offsets, 5, -4)
     g.close()
     assert_hits_equal(got, want, f"{world} GPU shards")
+
+
+# ---------------------------------------------------------------- MaxSSmap_fast (read step 2)
+@pytest.mark.parametrize("variant", [0, 1])
+def test_fast_step_tiny_50k(mss, variant):
+    """Every other read base: 50 kbp genome, 100 reads, both lane variants, with NW."""
+    wl = gen.workloads()["tiny-50k"]
+    genome, reads = gen.materialize(wl)
+    hits, alns, cig, oh, oa, oc = run_both(mss, genome, reads.seq, reads.offsets, wl.frag_len, wl.match,
+                                           wl.mismatch, nw=wl.nw, tune={"variant": variant}, procs=cpu_count(),
+                                           step=2)
+    assert_hits_equal(hits, oh, f"fast tiny-50k variant {variant}")
+    assert_alns_equal(alns, cig, oa, oc, f"fast tiny-50k variant {variant}")
+
+
+@pytest.mark.parametrize("match,mismatch", [(5, -4), (13, -4)])
+def test_fast_step_uneven_odd_lengths(mss, match, mismatch):
+    """Odd and even lengths (1 .. 700, several tiles and both selector-row sizes), N bases,
+    reads planted across fragment borders; 13 / -4 runs the int16 lanes, 5 / -4 the f16 lanes."""
+    wl = gen.scaled(gen.workloads()["bact-4.6M"], genome_len=60_000, reads=40)
+    genome, reads = gen.materialize(wl)
+    g_ascii = bytes(genome)
+    strs = [bytes(reads.read(i))[:L] for i, L in enumerate([1, 2, 3, 37, 100, 101, 150] * 5 + [149] * 5)]
+    strs += [g_ascii[4096 - 60:4096 + 61], g_ascii[20_000:20_333].replace(b"C", b"N", 9)]
+    long_reads = match == 13  # 5 x 400 <= 2048 keeps 5 / -4 on the f16 lanes
+    if long_reads:
+        strs.append(g_ascii[10_000:10_700])
+    seq, off = concat_reads(strs)
+    hits, _, _, oh, _, _ = run_both(mss, genome, seq, off, 2048, match, mismatch, max_len=700 if long_reads else 400,
+                                    procs=cpu_count(), step=2)
+    assert_hits_equal(hits, oh, f"fast uneven {match}/{mismatch}")
+
+
+def test_fast_step_device_graph_and_back_to_plain(mss):
+    """The device path replays its graph with step 2; switching back to step 1 gives the plain
+    results; bad steps and unsupported scan shapes are rejected."""
+    import torch
+    wl = gen.scaled(gen.workloads()["bact-4.6M"], genome_len=40_000, reads=24)
+    genome, reads = gen.materialize(wl)
+    g = mss.mss_load_genome(genome, frag_len=1024, max_read_len=150)
+    d_seq = torch.from_numpy(reads.seq).cuda()
+    d_off = torch.from_numpy(reads.offsets).cuda()
+    R = reads.count
+    s = torch.cuda.Stream()
+    mss.mss_set_read_step(g, 2)
+    assert mss.mss_get_read_step(g) == 2
+    want2, _, _ = oracle_map(genome, 1024, reads.seq, reads.offsets, 5, -4, procs=cpu_count(), step=2)
+    for _ in range(2):
+        d_hits = torch.zeros(R * 32, dtype=torch.uint8, device="cuda")
+        mss.mss_map_reads_device(g, d_seq, d_off, R, 150, 5, -4, d_hits, stream=s)
+        mss.mss_sync(g, stream=s)
+        assert_hits_equal(mss.hits_from_bytes(d_hits.cpu()), want2, "fast device")
+    mss.mss_set_read_step(g, 1)
+    want1, _, _ = oracle_map(genome, 1024, reads.seq, reads.offsets, 5, -4, procs=cpu_count())
+    assert_hits_equal(mss.mss_map_reads(g, reads.seq, reads.offsets, 5, -4), want1, "plain again")
+    with pytest.raises(mss.MssError):
+        mss.mss_set_read_step(g, 3)
+    mss.mss_set_read_step(g, 2)
+    mss.mss_set_tune(g, pairs=4, queries=8)
+    with pytest.raises(mss.MssError):
+        mss.mss_map_reads(g, reads.seq, reads.offsets, 5, -4)
+    g.close()
