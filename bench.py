@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-reads-per-core", type=int, default=2)
+    ap.add_argument("--autotune", action="store_true",
+                    help="pick the scan shape and fragment length with mss_autotune on a read sample first")
+    ap.add_argument("--autotune-reads", type=int, default=256)
     ap.add_argument("--read-step", type=int, default=1, choices=[1, 2],
                     help="2: MaxSSmap_fast (every other read base in phase one)")
     return ap.parse_args()
@@ -258,6 +261,19 @@ def main():
     d_cig = torch.empty(R * stride, dtype=torch.uint8, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
+    tuned = None
+    if args.autotune:
+        # an evenly spaced sample of the reads (all lengths), outside the timed region
+        n = min(R, args.autotune_reads)
+        s_seq, s_off = cpu_sample(seq, off, n)
+        t0 = time.perf_counter()
+        tuned = mss.mss_autotune(g, torch.from_numpy(s_seq).to(dev), torch.from_numpy(s_off).to(dev), n, max_len,
+                                 wl.match, wl.mismatch, allow_frag_len=True, stream=stream)
+        tuned["sample_reads"] = n
+        tuned["seconds"] = round(time.perf_counter() - t0, 1)
+        info = g.info()
+        cells_step = cells_of(lengths, genome.shape[0], info["frag_len"], args.read_step)
+
     def step():
         mss.mss_map_reads_device(g, d_seq, d_off, R, max_len, wl.match, wl.mismatch, d_hits, stream=stream)
         mss.nw_align_device(g, d_seq, d_off, R, max_len, d_hits, d_alns, d_cig, stride, nm, nmm, go, ge, W,
@@ -339,12 +355,12 @@ def main():
             "metric": METRIC, "value": round(gcups, 3), "unit": "GCUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(t * 1e3 / args.steps, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int16", "data": "synthetic",
-            "config": {"workload": wl.name, "genome_bp": int(genome.shape[0]), "frag_len": wl.frag_len,
+            "config": {"workload": wl.name, "genome_bp": int(genome.shape[0]), "frag_len": info["frag_len"],
                        "padded_bp": info["padded_len"], "reads": R, "read_lengths": sorted(set(lengths.tolist())),
                        "scores": [wl.match, wl.mismatch], "nw": list(wl.nw),
                        "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
                        "parallelism": f"replicas x{world} (read batches per GPU)", "scan_tune": tune,
-                       "read_step": args.read_step},
+                       "read_step": args.read_step, "autotune": tuned},
             "reads_per_s": round(reads_s, 1),
             "e2e": e2e,
             "gpu_launches": int(launches),

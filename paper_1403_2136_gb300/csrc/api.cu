@@ -254,9 +254,18 @@ mss_status enqueue_map(mss_ctx* c, const char* d_reads, const int64_t* d_offsets
     a.mm_word = a.prof_mismatch * 0x01010101u;
   }
   const int g = (int)std::max<int64_t>(1, std::min<int64_t>(grid, a.n_items));
-  if (c->timing) CK(cudaEventRecordWithFlags(c->ev_scan[0], s, cudaEventRecordExternal), "timing event");
+  // inside a stream capture the events become external event nodes of the graph; outside one
+  // they are recorded plainly
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (c->timing) CK(cudaStreamIsCapturing(s, &cap), "capture status");
+  const bool capturing = cap == cudaStreamCaptureStatusActive;
+  if (c->timing)
+    CK(capturing ? cudaEventRecordWithFlags(c->ev_scan[0], s, cudaEventRecordExternal) : cudaEventRecord(c->ev_scan[0], s),
+       "timing event");
   CK(launch_scan(cfg, a, g, smem, s), "scan kernel");
-  if (c->timing) CK(cudaEventRecordWithFlags(c->ev_scan[1], s, cudaEventRecordExternal), "timing event");
+  if (c->timing)
+    CK(capturing ? cudaEventRecordWithFlags(c->ev_scan[1], s, cudaEventRecordExternal) : cudaEventRecord(c->ev_scan[1], s),
+       "timing event");
   FinalArgs f{};
   f.g2 = c->pg.g2;
   f.gm = c->pg.gm;
@@ -666,12 +675,17 @@ mss_status mss_autotune(mss_ctx* c, const char* d_reads, const int64_t* d_offset
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0), "event");
   CK(cudaEventCreate(&e1), "event");
+  int timed = 0;
+  std::string last_failure;
   for (int64_t F : frags) {
     c->set_frag(F);
     for (const mss_tune& t : cands) {
       c->tune = t;
       st = map_device(c, d_reads, d_offsets, R, max_len, sp, (mss_hit*)hits.p, s, false);  // warm-up
-      if (st) continue;
+      if (st) {
+        last_failure = g_last_error;
+        continue;
+      }
       cudaEventRecord(e0, s);
       st = map_device(c, d_reads, d_offsets, R, max_len, sp, (mss_hit*)hits.p, s, false);
       cudaEventRecord(e1, s);
@@ -679,6 +693,7 @@ mss_status mss_autotune(mss_ctx* c, const char* d_reads, const int64_t* d_offset
       if (cudaEventSynchronize(e1) != cudaSuccess) continue;
       float ms = 0;
       cudaEventElapsedTime(&ms, e0, e1);
+      ++timed;
       if (ms < best_ms) {
         best_ms = ms;
         best = t;
@@ -691,6 +706,7 @@ mss_status mss_autotune(mss_ctx* c, const char* d_reads, const int64_t* d_offset
   c->tune = best;
   c->set_frag(bestF);
   hits.release();
+  if (timed == 0) return fail(MSS_ECUDA, "autotune: no candidate ran (%s)", last_failure.c_str());
   g_last_error.clear();
   return read_err(c, s);
 }

@@ -7,9 +7,7 @@
 //
 // Kernels (all here, the 128->128 contractions on tensor cores through mma.sync BF16):
 //   k_embed_l1      first layer (4 -> 128) as a gather-sum of per-base weight rows
-//   k_conv_mma      128 -> 128 conv as an implicit GEMM (7 shifted GEMMs, K = 128 per tap);
-//                   forward (bias + ReLU + length mask) and backward-data (flipped, transposed
-//                   weights; the epilogue applies the previous layer's ReLU mask)
+//   (the 128 -> 128 conv, forward and backward-data, runs on the tensor cores: conv_tc.cu)
 //   k_conv_wgrad    weight gradient, a GEMM over positions per tap (fp32 atomics across CTAs)
 //   k_pool_norm     max over positions (first argmax kept), L2 norm
 //   k_pool_norm_bwd gradient of the norm routed to the argmax positions
@@ -86,119 +84,12 @@ __global__ void k_embed_l1(const uint8_t* __restrict__ codes, const int32_t* __r
 }
 
 // ------------------------------------------------------------------------------------------
-// 128 -> 128 conv, one CTA = 128 positions x 128 output channels of one sequence.
-// in/out: [n][rows][128] bf16 (row = position + 3; rows outside [3, len + 3) are zero).
-// w: [7][128 ci][128 co] bf16.  mode 0: out = relu(acc + bias) masked to p < len.
-// mode 1 (backward data): out = acc where prev[n][p + 3][co] > 0 (and p < len), else 0.
+// shared-memory tiles of the weight-gradient GEMM (mma.sync): 134-row input tile + two 128-row
+// buffers of 256 bytes per row
 constexpr int kConvM = 128;
 constexpr int kConvThreads = 256;
 constexpr int kConvARows = kConvM + 6;
 constexpr size_t kConvSmem = (size_t)kConvARows * 256 + 2 * 128 * 256;
-
-__global__ void __launch_bounds__(kConvThreads, 2)
-    k_conv_mma(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ w,
-               const float* __restrict__ bias, const __nv_bfloat16* __restrict__ prev, const int32_t* __restrict__ lens,
-               __nv_bfloat16* __restrict__ out, int32_t rows, int mode) {
-  extern __shared__ __align__(128) uint8_t sm[];
-  const uint32_t sA = smem_u32(sm);
-  const uint32_t sW = sA + kConvARows * 256;
-  const int n = blockIdx.y, p0 = blockIdx.x * kConvM;
-  const int len = lens[n];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (p0 >= len) {  // whole tile beyond the sequence: write zeros
-    for (int e = tid; e < kConvM * 16; e += kConvThreads) {
-      const int r = e >> 4, c = e & 15;
-      if (p0 + r < rows - 6)
-        reinterpret_cast<uint4*>(out + ((int64_t)n * rows + p0 + r + 3) * kPropC)[c] = make_uint4(0, 0, 0, 0);
-    }
-    return;
-  }
-  const __nv_bfloat16* inb = in + ((int64_t)n * rows + p0) * kPropC;  // row p0 = position p0 - 3
-  for (int e = tid; e < kConvARows * 16; e += kConvThreads) {
-    const int r = e >> 4, c = e & 15;
-    cp_async16(sA + swz(r, c), inb + r * kPropC + c * 8);
-  }
-  auto load_w = [&](int t, int buf) {
-    const __nv_bfloat16* wt = w + (int64_t)t * kPropC * kPropC;
-    const uint32_t base = sW + buf * 128 * 256;
-    for (int e = tid; e < 128 * 16; e += kConvThreads) {
-      const int r = e >> 4, c = e & 15;
-      cp_async16(base + swz(r, c), wt + r * kPropC + c * 8);
-    }
-  };
-  load_w(0, 0);
-  cp_async_commit();
-
-  const int wm = warp & 3, wn = warp >> 2;  // warp tile: positions wm*32 + [0,32), channels wn*64 + [0,64)
-  float acc[2][8][4];
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 8; ++j)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
-
-  for (int t = 0; t < kPropTaps; ++t) {
-    if (t + 1 < kPropTaps) {
-      load_w(t + 1, (t + 1) & 1);
-      cp_async_commit();
-      cp_async_wait_1();
-    } else {
-      cp_async_wait_all();
-    }
-    __syncthreads();
-    const uint32_t wbase = sW + (t & 1) * 128 * 256;
-#pragma unroll
-    for (int kk = 0; kk < 8; ++kk) {  // 16 input channels per step
-      uint32_t af[2][4];
-#pragma unroll
-      for (int mi = 0; mi < 2; ++mi) {
-        const int i = lane >> 3;
-        const int r = wm * 32 + mi * 16 + (i & 1) * 8 + (lane & 7) + t;  // tap t shifts the rows
-        const int ch = kk * 2 + (i >> 1);
-        ldsm_x4(sA + swz(r, ch), af[mi][0], af[mi][1], af[mi][2], af[mi][3]);
-      }
-#pragma unroll
-      for (int nj = 0; nj < 8; nj += 2) {
-        const int i = lane >> 3;
-        const int r = kk * 16 + (i & 1) * 8 + (lane & 7);
-        const int ch = (wn * 64 + nj * 8) / 8 + (i >> 1);
-        uint32_t b0, b1, b2, b3;
-        ldsm_x4_t(wbase + swz(r, ch), b0, b1, b2, b3);
-#pragma unroll
-        for (int mi = 0; mi < 2; ++mi) {
-          mma_bf16(acc[mi][nj], af[mi], b0, b1);
-          mma_bf16(acc[mi][nj + 1], af[mi], b2, b3);
-        }
-      }
-    }
-    __syncthreads();  // the weight buffer of tap t is rewritten at t + 2
-  }
-  // epilogue
-#pragma unroll
-  for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-    for (int nj = 0; nj < 8; ++nj)
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int p = p0 + wm * 32 + mi * 16 + (lane >> 2) + h * 8;
-        const int co = wn * 64 + nj * 8 + (lane & 3) * 2;
-        if (p >= rows - 6) continue;
-        float v0 = acc[mi][nj][h * 2], v1 = acc[mi][nj][h * 2 + 1];
-        const int64_t o = ((int64_t)n * rows + p + 3) * kPropC + co;
-        if (p >= len) {
-          v0 = v1 = 0.f;
-        } else if (mode == 0) {
-          v0 = fmaxf(v0 + bias[co], 0.f);
-          v1 = fmaxf(v1 + bias[co + 1], 0.f);
-        } else {
-          const __nv_bfloat162 pv = *reinterpret_cast<const __nv_bfloat162*>(prev + o);
-          if (__bfloat162float(pv.x) <= 0.f) v0 = 0.f;
-          if (__bfloat162float(pv.y) <= 0.f) v1 = 0.f;
-        }
-        *reinterpret_cast<__nv_bfloat162*>(out + o) = __floats2bfloat162_rn(v0, v1);
-      }
-}
 
 // ------------------------------------------------------------------------------------------
 // weight gradient of a 128 -> 128 layer for one tap t: dw[t][ci][co] += sum_{n, p} in[n][p + t - 3][ci]
@@ -608,23 +499,15 @@ cudaError_t prop_embed_l1(const uint8_t* codes, const int32_t* lens, int32_t ld,
   return cudaGetLastError();
 }
 
-cudaError_t prop_conv(const __nv_bfloat16* in, const __nv_bfloat16* w, const float* bias, const __nv_bfloat16* prev,
-                      const int32_t* lens, __nv_bfloat16* out, int32_t n, int32_t rows, int mode, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_conv_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kConvSmem);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_conv_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kConvSmem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  dim3 grid((unsigned)((rows - 6) / kConvM), (unsigned)n);
-  k_conv_mma<<<grid, kConvThreads, kConvSmem, s>>>(in, w, bias, prev, lens, out, rows, mode);
-  return cudaGetLastError();
-}
 
 cudaError_t prop_conv_wgrad(const __nv_bfloat16* in, const __nv_bfloat16* g, const int32_t* lens, float* dw, int32_t n,
                             int32_t rows, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_conv_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kConvSmem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
   const int64_t total = (int64_t)n * ((rows - 6) / kConvM);
   const int64_t ctas = total < 64 ? total : 64;  // runs of tiles per tap
   const int32_t per = (int32_t)((total + ctas - 1) / ctas);

@@ -23,8 +23,15 @@ inline int32_t prop_rows(int32_t maxlen) { return ((maxlen + 127) / 128) * 128 +
 
 cudaError_t prop_embed_l1(const uint8_t* codes, const int32_t* lens, int32_t ld, int32_t n, const float* w1,
                           const float* b1, __nv_bfloat16* out, int32_t rows, cudaStream_t s);
-cudaError_t prop_conv(const __nv_bfloat16* in, const __nv_bfloat16* w, const float* bias, const __nv_bfloat16* prev,
-                      const int32_t* lens, __nv_bfloat16* out, int32_t n, int32_t rows, int mode, cudaStream_t s);
+// 128 -> 128 conv on the tensor cores (conv_tc.cu).  wcanon: the layer's weights w[t][in][out]
+// rearranged by prop_canon_weights (prop_canon_weight_bytes() bytes).  mode 0: out =
+// relu(conv + bias) for p < len; mode 1 (backward data, flipped weights): out = conv where
+// prev > 0.  err: device error word (a bounded wait that gives up sets ERR_TIMEOUT).
+int64_t prop_canon_weight_bytes();
+cudaError_t prop_canon_weights(const __nv_bfloat16* w, void* dst, cudaStream_t s);
+cudaError_t prop_conv_tc(const __nv_bfloat16* in, const void* wcanon, const float* bias, const __nv_bfloat16* prev,
+                         const int32_t* lens, __nv_bfloat16* out, int32_t n, int32_t rows, int mode, int32_t* err,
+                         cudaStream_t s);
 cudaError_t prop_conv_wgrad(const __nv_bfloat16* in, const __nv_bfloat16* g, const int32_t* lens, float* dw, int32_t n,
                             int32_t rows, cudaStream_t s);
 cudaError_t prop_bias_grad(const __nv_bfloat16* g, const int32_t* lens, float* db, int32_t n, int32_t rows,

@@ -70,6 +70,8 @@ struct Acts {
 struct mss_prop {
   Buf w32, m1, m2, grad;            // fp32 master weights, Adam moments, gradient (flat)
   Buf wb[3], wflip[3];              // bf16 weights of layers 2..4 and their flipped copies
+  Buf wct[3], wfct[3];              // the same as tensor-core B operands (conv_tc.cu layout)
+  Buf err;                          // device error word of the proposal kernels
   Acts fa, fb;                      // forward activations (reads / candidates) for training
   Buf g[2];                         // gradient activations (ping-pong)
   Buf loss, de_r, de_c;
@@ -89,7 +91,9 @@ mss_status refresh_bf16(mss_prop* p, cudaStream_t s) {
   for (int l = 2; l <= 4; ++l) {
     PCK(prop_to_bf16(p->w32.as<float>() + prop_off_w(l), p->wb[l - 2].as<__nv_bfloat16>(), kPropWl, s), "bf16 copy");
     PCK(prop_flip_weights(p->wb[l - 2].as<__nv_bfloat16>(), p->wflip[l - 2].as<__nv_bfloat16>(), s), "flip");
-    p->launches += 2;
+    PCK(prop_canon_weights(p->wb[l - 2].as<__nv_bfloat16>(), p->wct[l - 2].p, s), "weight layout");
+    PCK(prop_canon_weights(p->wflip[l - 2].as<__nv_bfloat16>(), p->wfct[l - 2].p, s), "weight layout");
+    p->launches += 4;
   }
   return MSS_OK;
 }
@@ -104,8 +108,8 @@ mss_status forward(mss_prop* p, const uint8_t* codes, const int32_t* lens, int32
   const float* w = p->w32.as<float>();
   PCK(prop_embed_l1(codes, lens, ld, n, w, w + prop_off_b1(), a.act[0].as<__nv_bfloat16>(), rows, s), "layer 1");
   for (int l = 2; l <= 4; ++l)
-    PCK(prop_conv(a.act[l - 2].as<__nv_bfloat16>(), p->wb[l - 2].as<__nv_bfloat16>(), w + prop_off_b(l), nullptr, lens,
-                  a.act[l - 1].as<__nv_bfloat16>(), n, rows, 0, s),
+    PCK(prop_conv_tc(a.act[l - 2].as<__nv_bfloat16>(), p->wct[l - 2].p, w + prop_off_b(l), nullptr, lens,
+                     a.act[l - 1].as<__nv_bfloat16>(), n, rows, 0, p->err.as<int32_t>(), s),
         "conv layer");
   PCK(prop_pool_norm(a.act[3].as<__nv_bfloat16>(), lens, n, rows, a.emb.as<float>(), a.norms.as<float>(),
                      a.argmax.as<int32_t>(), s),
@@ -134,8 +138,8 @@ mss_status backward(mss_prop* p, const uint8_t* codes, const int32_t* lens, int3
     // gcur = gradient of layer l's pre-activation; input activation of layer l is act[l - 2]
     PCK(prop_conv_wgrad(a.act[l - 2].as<__nv_bfloat16>(), gcur, lens, gw + prop_off_w(l), n, rows, s), "wgrad");
     PCK(prop_bias_grad(gcur, lens, gw + prop_off_b(l), n, rows, s), "bias grad");
-    PCK(prop_conv(gcur, p->wflip[l - 2].as<__nv_bfloat16>(), nullptr, a.act[l - 2].as<__nv_bfloat16>(), lens, gnext, n,
-                  rows, 1, s),
+    PCK(prop_conv_tc(gcur, p->wfct[l - 2].p, nullptr, a.act[l - 2].as<__nv_bfloat16>(), lens, gnext, n, rows, 1,
+                     p->err.as<int32_t>(), s),
         "conv backward");
     std::swap(gcur, gnext);
     p->launches += 3;
@@ -143,6 +147,16 @@ mss_status backward(mss_prop* p, const uint8_t* codes, const int32_t* lens, int3
   PCK(prop_l1_wgrad(codes, lens, ld, gcur, gw, gw + prop_off_b1(), n, rows, s), "layer 1 grad");
   p->launches += 1;
   return MSS_OK;
+}
+
+// Synchronize and read (then clear) the proposal kernels' error word.
+mss_status read_prop_err(mss_prop* p, cudaStream_t s) {
+  int32_t h = 0;
+  PCK(cudaStreamSynchronize(s), "sync");
+  PCK(cudaMemcpy(&h, p->err.p, sizeof(int32_t), cudaMemcpyDeviceToHost), "error word read");
+  if (h == 0) return MSS_OK;
+  PCK(cudaMemset(p->err.p, 0, sizeof(int32_t)), "error word clear");
+  return set_error(MSS_ETIMEOUT, "a bounded wait of a tensor-core kernel gave up");
 }
 
 mss_status check_prop(const mss_prop* p) {
@@ -178,7 +192,11 @@ mss_status mss_prop_create(mss_prop** out, uint64_t seed, void* stream) {
   for (int l = 0; l < 3 && e == cudaSuccess; ++l) {
     e = p->wb[l].ensure((size_t)kPropWl * 2);
     if (e == cudaSuccess) e = p->wflip[l].ensure((size_t)kPropWl * 2);
+    if (e == cudaSuccess) e = p->wct[l].ensure((size_t)prop_canon_weight_bytes());
+    if (e == cudaSuccess) e = p->wfct[l].ensure((size_t)prop_canon_weight_bytes());
   }
+  if (e == cudaSuccess) e = p->err.ensure(sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->err.p, 0, sizeof(int32_t), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(p->m1.p, 0, pb, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(p->m2.p, 0, pb, s);
   if (e == cudaSuccess) e = prop_init_params(p->w32.as<float>(), seed, s);
@@ -200,11 +218,13 @@ void mss_prop_free(mss_prop* p) {
   if (!p) return;
   for (Buf* b : {&p->w32, &p->m1, &p->m2, &p->grad, &p->loss, &p->de_r, &p->de_c, &p->codes, &p->lens, &p->starts,
                  &p->idx, &p->strand, &p->index, &p->scores, &p->cand, &p->cand_s, &p->emb_reads, &p->g[0], &p->g[1],
-                 &p->cand_x, &p->breads, &p->part_key, &p->part_f})
+                 &p->cand_x, &p->breads, &p->part_key, &p->part_f, &p->err})
     b->release();
   for (int l = 0; l < 3; ++l) {
     p->wb[l].release();
     p->wflip[l].release();
+    p->wct[l].release();
+    p->wfct[l].release();
   }
   for (Acts* a : {&p->fa, &p->fb}) {
     for (auto& b : a->act) b.release();
@@ -293,7 +313,8 @@ mss_status mss_prop_train_step(mss_prop* p, const uint8_t* d_rcodes, const int32
   if (loss_out) {
     std::vector<float> h(B);
     PCK(cudaMemcpyAsync(h.data(), p->loss.p, (size_t)B * 4, cudaMemcpyDeviceToHost, s), "loss read");
-    PCK(cudaStreamSynchronize(s), "sync");
+    st = read_prop_err(p, s);
+    if (st) return st;
     double sum = 0;
     for (float v : h) sum += v;
     *loss_out = (float)(sum / B);
@@ -341,6 +362,10 @@ mss_status mss_prop_build_index(mss_prop* p, mss_ctx* ctx, int32_t max_read_len,
     p->launches += 2;
   }
   tmp.release();
+  {
+    mss_status est = read_prop_err(p, s);
+    if (est) return est;
+  }
   p->index_nf = NF;
   p->index_F = F;
   p->index_window = win;
@@ -440,6 +465,7 @@ mss_status mss_map_reads_proposed(mss_ctx* ctx, mss_prop* p, const char* d_reads
   PCK(cudaMemcpyAsync(top.data(), p->cand_s.p, (size_t)R * K * 4, cudaMemcpyDeviceToHost, s), "scores read");
   {
     mss_status est = mss_sync(ctx, stream);  // synchronizes; reports bad characters / lengths
+    if (!est) est = read_prop_err(p, s);
     if (est) return est;
   }
   if (d_top_score) {

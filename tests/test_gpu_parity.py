@@ -208,6 +208,13 @@ def test_autotune_keeps_results(mss):
     assert t["frag_len"] == 2048
     after = mss.mss_map_reads(g, reads.seq, reads.offsets, 5, -4)
     assert_hits_equal(after, before, "autotune")
+    # with scan timing on (as in the benchmark) and the fragment length free: the candidates run
+    # outside graph capture, the chosen F is one of the candidates, results follow the new F
+    mss.mss_scan_timing(g, True)
+    t = mss.mss_autotune(g, d_seq, d_off, reads.count, 150, 5, -4, allow_frag_len=True)
+    assert t["frag_len"] in (1024, 2048, 4096, 8192) and t["variant"] in (0, 1) and t["pairs"] in (4, 8)
+    want, _, _ = oracle_map(genome, t["frag_len"], reads.seq, reads.offsets, 5, -4, procs=cpu_count())
+    assert_hits_equal(mss.mss_map_reads(g, reads.seq, reads.offsets, 5, -4), want, "autotuned F")
     g.close()
 
 

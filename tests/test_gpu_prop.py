@@ -339,7 +339,8 @@ def test_training_step_and_checkpoint(mss):
     losses = [prop.train_step(d[0], d[1], Lr, B, Lr, d[2], d[3], Lc, C, Lc, d[4], lr=3e-3, temperature=0.1)
               for _ in range(25)]
     assert abs(losses[0] - want_loss) < 5e-2 * max(1.0, abs(want_loss)), (losses[0], want_loss)
-    assert losses[-1] < losses[0] * 0.8, losses
+    # the fixed batch is learned (Adam at this rate then oscillates around the minimum)
+    assert min(losses) < losses[0] * 0.5, losses
     with tempfile.TemporaryDirectory() as td:
         path = os.path.join(td, "prop.ckpt")
         prop.save(path)
