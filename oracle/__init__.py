@@ -29,7 +29,7 @@ def build(force: bool = False) -> str:
     newest = max(os.path.getmtime(src), os.path.getmtime(hdr))
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < newest:
         tmp = _SO + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, src])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, src, "-lm"])
         os.replace(tmp, _SO)
     return _SO
 
@@ -65,6 +65,12 @@ def _lib():
             lib.orc_diag_score_step.restype = i32
             lib.orc_map_read.argtypes = [P, i64, i64, P, i32, i32, i32, ctypes.POINTER(Hit), P]
             lib.orc_map_read_step.argtypes = [P, i64, i64, P, i32, i32, i32, i32, ctypes.POINTER(Hit), P]
+            lib.orc_pssm_scores.argtypes = [i32, i32, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+            lib.orc_map_read_pssm.argtypes = [P, i64, i64, P, P, i32, i32, i32, i32, ctypes.POINTER(Hit), P]
+            lib.orc_nw_banded_pssm.argtypes = [P, i64, P, P, P, i32, i64, i32, i32, i32, ctypes.POINTER(Aln),
+                                               ctypes.c_char_p, i32]
+            lib.orc_map_batch_pssm.argtypes = [P, i64, i64, P, P, P, i32, i32, i32, i32, i32, i32, i32, i32, i32,
+                                               P, P, P, i32]
             lib.orc_revcomp.argtypes = [P, i32, P]
             lib.orc_revcomp.restype = None
             lib.orc_encode.argtypes = [P, i64, P]
@@ -125,13 +131,42 @@ def diag_score(qcodes, gcodes_padded, d: int, match: int, mismatch: int, step: i
     return int(_lib().orc_diag_score_step(_p(q), q.shape[0], _p(g), d, match, mismatch, step))
 
 
-def map_read(genome, F: int, read, match: int, mismatch: int, with_frag_scores: bool = False, step: int = 1):
+def pssm_scores(qual_char: int, match: int, mismatch: int, scale: int):
+    """(match, mismatch) of a base with Phred+33 quality character qual_char, in fixed point."""
+    a, b = ctypes.c_int32(), ctypes.c_int32()
+    if _lib().orc_pssm_scores(int(qual_char), match, mismatch, scale, ctypes.byref(a), ctypes.byref(b)) != 0:
+        raise ValueError("bad quality character or scale")
+    return a.value, b.value
+
+
+def nw_banded_pssm(gcodes, qcodes, ma, mm, d: int, W: int, gap_open: int, gap_extend: int, cigar_cap: int = 4096):
+    g = np.ascontiguousarray(gcodes, dtype=np.uint8)
+    q = np.ascontiguousarray(qcodes, dtype=np.uint8)
+    a_ = np.ascontiguousarray(ma, dtype=np.int32)
+    m_ = np.ascontiguousarray(mm, dtype=np.int32)
+    a = Aln()
+    buf = ctypes.create_string_buffer(cigar_cap)
+    rc = _lib().orc_nw_banded_pssm(_p(g), g.shape[0], _p(q), _p(a_), _p(m_), q.shape[0], d, W, gap_open, gap_extend,
+                                   ctypes.byref(a), buf, cigar_cap)
+    if rc != 0:
+        raise ValueError(f"orc_nw_banded_pssm failed ({rc})")
+    return a.score, a.gstart, a.gend, buf.value.decode()
+
+
+def map_read(genome, F: int, read, match: int, mismatch: int, with_frag_scores: bool = False, step: int = 1,
+             quals=None, scale: int = 4):
+    """quals (Phred+33, one per read base): position-specific scores with the given fixed-point scale."""
     g = _buf(genome)
     r = _buf(read)
     h = Hit()
     NF = (g.shape[0] + F - 1) // F
     fs = np.empty(NF, dtype=np.int32) if with_frag_scores else None
-    if step == 1:
+    if quals is not None:
+        qb = _buf(quals)
+        assert qb.shape[0] == r.shape[0]
+        rc = _lib().orc_map_read_pssm(_p(g), g.shape[0], F, _p(r), _p(qb), r.shape[0], match, mismatch, scale,
+                                      ctypes.byref(h), _p(fs) if fs is not None else None)
+    elif step == 1:
         rc = _lib().orc_map_read(_p(g), g.shape[0], F, _p(r), r.shape[0], match, mismatch, ctypes.byref(h),
                                  _p(fs) if fs is not None else None)
     else:
@@ -174,7 +209,7 @@ ALN_DTYPE = np.dtype([("score", np.int32), ("cigar_len", np.int32), ("gstart", n
 
 
 def map_batch(genome, F: int, reads: np.ndarray, offsets: np.ndarray, match: int, mismatch: int,
-              nw=None, cigar_cap: int = 1024, step: int = 1):
+              nw=None, cigar_cap: int = 1024, step: int = 1, quals=None, scale: int = 4):
     """Phase one (and phase two when nw = (match, mismatch, open, extend, W)) for a batch.
     Returns (hits structured array, alns structured array or None, list of CIGAR strings or None)."""
     g = _buf(genome)
@@ -185,9 +220,16 @@ def map_batch(genome, F: int, reads: np.ndarray, offsets: np.ndarray, match: int
     alns = np.zeros(R, dtype=ALN_DTYPE) if nw is not None else None
     cig = np.zeros((R, cigar_cap), dtype=np.uint8) if nw is not None else None
     nm, nmm, go, ge, W = nw if nw is not None else (0, 0, 0, 0, 0)
-    rc = _lib().orc_map_batch_step(_p(g), g.shape[0], F, _p(rd), _p(off), R, match, mismatch, step, nm, nmm, go,
-                                   ge, W, _p(hits), _p(alns) if alns is not None else None,
-                                   _p(cig) if cig is not None else None, cigar_cap)
+    if quals is not None:
+        qd = np.ascontiguousarray(quals, dtype=np.uint8)
+        assert qd.shape[0] == rd.shape[0]
+        rc = _lib().orc_map_batch_pssm(_p(g), g.shape[0], F, _p(rd), _p(qd), _p(off), R, match, mismatch, scale, nm,
+                                       nmm, go, ge, W, _p(hits), _p(alns) if alns is not None else None,
+                                       _p(cig) if cig is not None else None, cigar_cap)
+    else:
+        rc = _lib().orc_map_batch_step(_p(g), g.shape[0], F, _p(rd), _p(off), R, match, mismatch, step, nm, nmm, go,
+                                       ge, W, _p(hits), _p(alns) if alns is not None else None,
+                                       _p(cig) if cig is not None else None, cigar_cap)
     if rc != 0:
         raise ValueError(f"orc_map_batch failed ({rc})")
     cigars = None

@@ -5,6 +5,7 @@
  */
 #include "oracle.h"
 
+#include <math.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -53,14 +54,20 @@ int64_t orc_mss(const int32_t* x, int64_t n) {
 /* substitution scores of the read against the genome window that starts at diagonal d, at
    read positions 0, step, 2 step, ... (step 1: every base; step 2: "MaxSSmap_fast", every other
    nucleotide of the read); returns how many scores were written */
-static int32_t diag_scores(const uint8_t* q, int32_t m, const uint8_t* g, int64_t d, int32_t match,
-                           int32_t mismatch, int32_t step, int32_t* x) {
+static int32_t diag_scores_pos(const uint8_t* q, int32_t m, const uint8_t* g, int64_t d, int32_t match,
+                               int32_t mismatch, int32_t step, const int32_t* ma, const int32_t* mm, int32_t* x) {
   int32_t n = 0;
   for (int32_t k = 0; k < m; k += step) {
     uint8_t a = q[k], b = g[d + k];
-    x[n++] = (a < 4 && a == b) ? match : mismatch;
+    int32_t sm = ma ? ma[k] : match, sx = mm ? mm[k] : mismatch; /* position-specific when given */
+    x[n++] = (a < 4 && a == b) ? sm : sx;
   }
   return n;
+}
+
+static int32_t diag_scores(const uint8_t* q, int32_t m, const uint8_t* g, int64_t d, int32_t match,
+                           int32_t mismatch, int32_t step, int32_t* x) {
+  return diag_scores_pos(q, m, g, d, match, mismatch, step, 0, 0, x);
 }
 
 /* One ungapped read-vs-genome diagonal ("First phase of MaxSSmap"): the substitution score
@@ -84,8 +91,56 @@ int orc_map_read(const char* genome, int64_t G, int64_t F, const char* read, int
   return orc_map_read_step(genome, G, F, read, m, match, mismatch, 1, out, frag_scores);
 }
 
+static int map_read_impl(const char* genome, int64_t G, int64_t F, const char* read, int32_t m, int32_t match,
+                         int32_t mismatch, int32_t step, const int32_t* const* ma, const int32_t* const* mm,
+                         orc_hit* out, int32_t* frag_scores);
+
 int orc_map_read_step(const char* genome, int64_t G, int64_t F, const char* read, int32_t m, int32_t match,
                       int32_t mismatch, int32_t step, orc_hit* out, int32_t* frag_scores) {
+  return map_read_impl(genome, G, F, read, m, match, mismatch, step, 0, 0, out, frag_scores);
+}
+
+/* "Incorporating base qualities and position specific scoring matrix": a base of Phred
+   quality Q is right with probability x = 1 - 10^(-Q/10); a match against it scores
+   match * x and a mismatch mismatch * x / 3.  Fixed point: both times scale, rounded to the
+   nearest integer with halves away from zero. */
+static int32_t round_half_away(double v) { return (int32_t)(v < 0 ? -floor(-v + 0.5) : floor(v + 0.5)); }
+
+int orc_pssm_scores(int32_t qual_char, int32_t match, int32_t mismatch, int32_t scale, int32_t* ma, int32_t* mm) {
+  int32_t Q = qual_char - 33; /* Phred+33 */
+  if (Q < 0 || Q > 93 || scale < 1) return -1;
+  double x = 1.0 - pow(10.0, -Q / 10.0);
+  *ma = round_half_away((double)scale * match * x);
+  *mm = round_half_away((double)scale * mismatch * x / 3.0);
+  return 0;
+}
+
+int orc_map_read_pssm(const char* genome, int64_t G, int64_t F, const char* read, const char* quals, int32_t m,
+                      int32_t match, int32_t mismatch, int32_t scale, orc_hit* out, int32_t* frag_scores) {
+  if (m <= 0 || !quals) return -1;
+  int32_t* buf = (int32_t*)malloc(sizeof(int32_t) * 4 * (size_t)m);
+  if (!buf) return -2;
+  int32_t *maf = buf, *mmf = buf + m, *mar = buf + 2 * m, *mmr = buf + 3 * m;
+  for (int32_t k = 0; k < m; ++k) {
+    if (orc_pssm_scores((unsigned char)quals[k], match, mismatch, scale, &maf[k], &mmf[k]) != 0) {
+      free(buf);
+      return -1;
+    }
+  }
+  for (int32_t k = 0; k < m; ++k) { /* the reverse complement's base k is read base m - 1 - k */
+    mar[k] = maf[m - 1 - k];
+    mmr[k] = mmf[m - 1 - k];
+  }
+  const int32_t* ma[2] = {maf, mar};
+  const int32_t* mm[2] = {mmf, mmr};
+  int rc = map_read_impl(genome, G, F, read, m, match, mismatch, 1, ma, mm, out, frag_scores);
+  free(buf);
+  return rc;
+}
+
+static int map_read_impl(const char* genome, int64_t G, int64_t F, const char* read, int32_t m, int32_t match,
+                         int32_t mismatch, int32_t step, const int32_t* const* ma, const int32_t* const* mm,
+                         orc_hit* out, int32_t* frag_scores) {
   if (G <= 0 || F <= 0 || m <= 0 || !out || (step != 1 && step != 2)) return -1;
   int64_t NF = (G + F - 1) / F;
   int64_t Gp = NF * F;
@@ -112,7 +167,7 @@ int orc_map_read_step(const char* genome, int64_t G, int64_t F, const char* read
      bases up to (f+1)F + m - 1 (the junction into the right neighbour) */
   for (int32_t sg = 0; sg < 2; ++sg) {
     for (int64_t d = 0; d < Gp; ++d) {
-      int32_t n = diag_scores(q[sg], m, g, d, match, mismatch, step, x);
+      int32_t n = diag_scores_pos(q[sg], m, g, d, match, mismatch, step, ma ? ma[sg] : 0, mm ? mm[sg] : 0, x);
       int32_t K = (int32_t)orc_mss(x, n);
       int64_t f = d / F;
       if (K > S[f]) { /* strictly greater: + strand before -, then the smallest d */
@@ -178,8 +233,8 @@ static int append_run(char* cigar, int32_t cap, int32_t* len, int32_t n, char op
 /* w: window codes [0..L), q: read codes [0..m), off: window column of read base 0 on the
    seed diagonal, W < 0: unbanded. */
 static int nw_core(const uint8_t* w, int64_t L, const uint8_t* q, int32_t m, int64_t off, int64_t W, int32_t match,
-                   int32_t mismatch, int32_t gap_open, int32_t gap_extend, int64_t wstart, orc_aln* out, char* cigar,
-                   int32_t cigar_cap) {
+                   int32_t mismatch, const int32_t* ma, const int32_t* mm, int32_t gap_open, int32_t gap_extend,
+                   int64_t wstart, orc_aln* out, char* cigar, int32_t cigar_cap) {
   int64_t cols = L + 1;
   int64_t cells = (int64_t)(m + 1) * cols;
   int64_t* H = (int64_t*)malloc(sizeof(int64_t) * (size_t)cells);
@@ -202,7 +257,7 @@ static int nw_core(const uint8_t* w, int64_t L, const uint8_t* q, int32_t m, int
       int64_t diag = NEG_INF, e = NEG_INF, f;
       if (j >= 1) {
         uint8_t a = q[i - 1], b = w[j - 1];
-        int32_t s = (a < 4 && a == b) ? match : mismatch;
+        int32_t s = (a < 4 && a == b) ? (ma ? ma[i - 1] : match) : (mm ? mm[i - 1] : mismatch);
         if (AT(H, i - 1, j - 1) > NEG_INF / 2) diag = AT(H, i - 1, j - 1) + s;
         e = max2(AT(H, i, j - 1) + gap_open, AT(E, i, j - 1) + gap_extend);
       }
@@ -238,7 +293,7 @@ static int nw_core(const uint8_t* w, int64_t L, const uint8_t* q, int32_t m, int
       int64_t h = AT(H, i, j);
       if (j >= 1 && AT(H, i - 1, j - 1) > NEG_INF / 2) {
         uint8_t a = q[i - 1], b = w[j - 1];
-        int32_t s = (a < 4 && a == b) ? match : mismatch;
+        int32_t s = (a < 4 && a == b) ? (ma ? ma[i - 1] : match) : (mm ? mm[i - 1] : mismatch);
         if (h == AT(H, i - 1, j - 1) + s) {
           ops[nops++] = 'M';
           --i; --j;
@@ -291,7 +346,24 @@ int orc_nw_banded(const uint8_t* gcodes, int64_t G, const uint8_t* q, int32_t m,
   int64_t L = we - ws;
   if (L < 0) L = 0;
   int64_t off = d - ws;
-  return nw_core(gcodes + ws, L, q, m, off, W, match, mismatch, gap_open, gap_extend, ws, out, cigar, cigar_cap);
+  return nw_core(gcodes + ws, L, q, m, off, W, match, mismatch, 0, 0, gap_open, gap_extend, ws, out, cigar,
+                 cigar_cap);
+}
+
+/* the banded reading with position-specific match / mismatch scores of the read bases
+   (ma[i], mm[i] for read base i; gaps as given, already in the same fixed point) */
+int orc_nw_banded_pssm(const uint8_t* gcodes, int64_t G, const uint8_t* q, const int32_t* ma, const int32_t* mm,
+                       int32_t m, int64_t d, int32_t W, int32_t gap_open, int32_t gap_extend, orc_aln* out,
+                       char* cigar, int32_t cigar_cap) {
+  if (G <= 0 || m <= 0 || W < 0 || d < 0 || !out || !ma || !mm) return -1;
+  int64_t ws = d - W;
+  if (ws < 0) ws = 0;
+  int64_t we = d + m + W;
+  if (we > G) we = G;
+  int64_t L = we - ws;
+  if (L < 0) L = 0;
+  int64_t off = d - ws;
+  return nw_core(gcodes + ws, L, q, m, off, W, 0, 0, ma, mm, gap_open, gap_extend, ws, out, cigar, cigar_cap);
 }
 
 int orc_nw_literal(const uint8_t* gcodes, int64_t G, int64_t F, int32_t best_frag, const uint8_t* q, int32_t m,
@@ -303,7 +375,7 @@ int orc_nw_literal(const uint8_t* gcodes, int64_t G, int64_t F, int32_t best_fra
   int64_t we = ws + nfr * F;
   if (we > G) we = G;
   if (ws > G) ws = G;
-  return nw_core(gcodes + ws, we - ws, q, m, 0, -1, match, mismatch, gap_open, gap_extend, ws, out, cigar,
+  return nw_core(gcodes + ws, we - ws, q, m, 0, -1, match, mismatch, 0, 0, gap_open, gap_extend, ws, out, cigar,
                  cigar_cap);
 }
 
@@ -333,6 +405,46 @@ int orc_map_batch_step(const char* genome, int64_t G, int64_t F, const char* rea
       rc = orc_nw_banded(g, G, qs, m, hits[r].offset, W, nw_match, nw_mismatch, gap_open, gap_extend, &alns[r],
                          cigars ? cigars + (int64_t)r * cigar_cap : 0, cigars ? cigar_cap : 0);
       free(q); free(qs);
+      if (rc != 0) { free(g); return rc; }
+    }
+  }
+  free(g);
+  return 0;
+}
+
+/* Both phases with base qualities (quals: Phred+33, same offsets as the reads; scale: the
+   fixed point of the scores; phase two gaps are multiplied by scale). */
+int orc_map_batch_pssm(const char* genome, int64_t G, int64_t F, const char* reads, const char* quals,
+                       const int64_t* offsets, int32_t R, int32_t match, int32_t mismatch, int32_t scale,
+                       int32_t nw_match, int32_t nw_mismatch, int32_t gap_open, int32_t gap_extend, int32_t W,
+                       orc_hit* hits, orc_aln* alns, char* cigars, int32_t cigar_cap) {
+  uint8_t* g = (uint8_t*)malloc((size_t)G);
+  if (!g) return -2;
+  if (orc_encode(genome, G, g) != 0) { free(g); return -1; }
+  for (int32_t r = 0; r < R; ++r) {
+    int32_t m = (int32_t)(offsets[r + 1] - offsets[r]);
+    int rc = orc_map_read_pssm(genome, G, F, reads + offsets[r], quals + offsets[r], m, match, mismatch, scale,
+                               &hits[r], 0);
+    if (rc != 0) { free(g); return rc; }
+    if (alns) {
+      uint8_t* q = (uint8_t*)malloc((size_t)m);
+      uint8_t* qs = (uint8_t*)malloc((size_t)m);
+      int32_t* sc = (int32_t*)malloc(sizeof(int32_t) * 4 * (size_t)m);
+      int32_t *ma = sc, *mm = sc + m, *mas = sc + 2 * m, *mms = sc + 3 * m;
+      orc_encode(reads + offsets[r], m, q);
+      for (int32_t k = 0; k < m; ++k)
+        orc_pssm_scores((unsigned char)quals[offsets[r] + k], nw_match, nw_mismatch, scale, &ma[k], &mm[k]);
+      if (hits[r].strand == 1) {
+        orc_revcomp(q, m, qs);
+        for (int32_t k = 0; k < m; ++k) { mas[k] = ma[m - 1 - k]; mms[k] = mm[m - 1 - k]; }
+      } else {
+        memcpy(qs, q, (size_t)m);
+        memcpy(mas, ma, sizeof(int32_t) * (size_t)m);
+        memcpy(mms, mm, sizeof(int32_t) * (size_t)m);
+      }
+      rc = orc_nw_banded_pssm(g, G, qs, mas, mms, m, hits[r].offset, W, gap_open * scale, gap_extend * scale,
+                              &alns[r], cigars ? cigars + (int64_t)r * cigar_cap : 0, cigars ? cigar_cap : 0);
+      free(q); free(qs); free(sc);
       if (rc != 0) { free(g); return rc; }
     }
   }

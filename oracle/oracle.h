@@ -80,6 +80,17 @@ int orc_map_read(const char* genome, int64_t G, int64_t F, const char* read, int
 int orc_map_read_step(const char* genome, int64_t G, int64_t F, const char* read, int32_t m, int32_t match,
                       int32_t mismatch, int32_t step, orc_hit* out, int32_t* frag_scores);
 
+/* Base qualities ("Incorporating base qualities and position specific scoring matrix"):
+   x = 1 - 10^(-Q/10) for Phred+33 quality character qual_char; *ma = match * x * scale and
+   *mm = mismatch * x / 3 * scale, rounded to the nearest integer (halves away from zero).
+   Returns -1 for a character outside '!'..'~' or scale < 1. */
+int orc_pssm_scores(int32_t qual_char, int32_t match, int32_t mismatch, int32_t scale, int32_t* ma, int32_t* mm);
+
+/* phase one with those position-specific scores (read base k of the reverse complement takes
+   the quality of read base m - 1 - k); N never matches and scores the position's mismatch */
+int orc_map_read_pssm(const char* genome, int64_t G, int64_t F, const char* read, const char* quals, int32_t m,
+                      int32_t match, int32_t mismatch, int32_t scale, orc_hit* out, int32_t* frag_scores);
+
 /* reverse complement of codes (4 stays 4) */
 void orc_revcomp(const uint8_t* q, int32_t m, uint8_t* out);
 
@@ -122,6 +133,13 @@ int orc_encode(const char* s, int64_t n, uint8_t* out);
 int orc_map_batch(const char* genome, int64_t G, int64_t F, const char* reads, const int64_t* offsets, int32_t R,
                   int32_t match, int32_t mismatch, int32_t nw_match, int32_t nw_mismatch, int32_t gap_open,
                   int32_t gap_extend, int32_t W, orc_hit* hits, orc_aln* alns, char* cigars, int32_t cigar_cap);
+int orc_nw_banded_pssm(const uint8_t* gcodes, int64_t G, const uint8_t* q, const int32_t* ma, const int32_t* mm,
+                       int32_t m, int64_t d, int32_t W, int32_t gap_open, int32_t gap_extend, orc_aln* out,
+                       char* cigar, int32_t cigar_cap);
+int orc_map_batch_pssm(const char* genome, int64_t G, int64_t F, const char* reads, const char* quals,
+                       const int64_t* offsets, int32_t R, int32_t match, int32_t mismatch, int32_t scale,
+                       int32_t nw_match, int32_t nw_mismatch, int32_t gap_open, int32_t gap_extend, int32_t W,
+                       orc_hit* hits, orc_aln* alns, char* cigars, int32_t cigar_cap);
 int orc_map_batch_step(const char* genome, int64_t G, int64_t F, const char* reads, const int64_t* offsets,
                        int32_t R, int32_t match, int32_t mismatch, int32_t step, int32_t nw_match,
                        int32_t nw_mismatch, int32_t gap_open, int32_t gap_extend, int32_t W, orc_hit* hits,

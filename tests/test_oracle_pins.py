@@ -326,13 +326,14 @@ def test_paper_closed_forms():
 
 
 # ---------------------------------------------------------------- phase two
-def alignment_score(read, window, ops, match, mismatch, go, ge):
+def alignment_score(read, window, ops, match, mismatch, go, ge, pos=None):
+    """pos = (ma, mm): position-specific match / mismatch scores of the read bases."""
     i = j = 0
     score = 0
     prev = None
     for op in ops:
         if op == "M":
-            score += sub_score(read[i], window[j], match, mismatch)
+            score += sub_score(read[i], window[j], *((pos[0][i], pos[1][i]) if pos else (match, mismatch)))
             i += 1
             j += 1
         elif op == "I":
@@ -345,7 +346,7 @@ def alignment_score(read, window, ops, match, mismatch, go, ge):
     return score, i, j
 
 
-def brute_glocal(read, window, match, mismatch, go, ge):
+def brute_glocal(read, window, match, mismatch, go, ge, pos=None):
     """Best glocal alignment by enumeration: every genome start, every op string."""
     m, L = len(read), len(window)
     best = None
@@ -359,7 +360,8 @@ def brute_glocal(read, window, match, mismatch, go, ge):
                     best = score
                 # trailing genome bases are free: stop here
             if i < m and j < len(sub):
-                rec(i + 1, j + 1, "M", score + sub_score(read[i], sub[j], match, mismatch))
+                sm, sx = (pos[0][i], pos[1][i]) if pos else (match, mismatch)
+                rec(i + 1, j + 1, "M", score + sub_score(read[i], sub[j], sm, sx))
             if i < m:
                 rec(i + 1, j, "I", score + (ge if prev == "I" else go))
             if j < len(sub) and i < m:   # a deletion must be followed by more read (trailing ones are free)
@@ -435,3 +437,116 @@ def test_nw_literal_region():
     read = genome[130:170]   # inside fragment 2 (128..191)
     sc, gs, ge, cig = oracle.nw_literal(oracle.encode(genome), F, 2, oracle.encode(read), 5, -4, -26, -26)
     assert (sc, gs, ge, cig) == (200, 130, 170, "40M")
+
+
+# ---------------------------------------------------------------- base qualities (PSSM)
+def pssm_py(qchar: int, match: int, mismatch: int, scale: int):
+    """The paper's scores written out again in Python: x = 1 - 10^(-Q/10), match * x and
+    mismatch * x / 3, times scale, rounded half away from zero."""
+    x = 1.0 - 10.0 ** (-(qchar - 33) / 10.0)
+
+    def rnd(v):
+        return int(math.floor(v + 0.5)) if v >= 0 else -int(math.floor(-v + 0.5))
+    return rnd(scale * match * x), rnd(scale * mismatch * x / 3.0)
+
+
+def test_pssm_scores_closed_forms():
+    # Q 40: x = 0.9999; Q 20: 0.99; Q 10: 0.9; Q 3: 0.4988; Q 0: 0 (scale 4, 5 / -4)
+    assert oracle.pssm_scores(ord("I"), 5, -4, 4) == (20, -5)
+    assert oracle.pssm_scores(ord("5"), 5, -4, 4) == (20, -5)      # 19.8, -5.28
+    assert oracle.pssm_scores(ord("+"), 5, -4, 4) == (18, -5)      # 18.0, -4.8
+    assert oracle.pssm_scores(ord("$"), 5, -4, 4) == (10, -3)      # 9.976, -2.66
+    assert oracle.pssm_scores(ord("!"), 5, -4, 4) == (0, 0)
+    assert oracle.pssm_scores(ord("?"), 3, -3, 1) == (3, -1)       # Q 30: 2.997, -0.999
+    for q in range(33, 127):
+        for (ma, mm, sc) in [(5, -4, 4), (1, -1, 8), (2, -3, 1)]:
+            assert oracle.pssm_scores(q, ma, mm, sc) == pssm_py(q, ma, mm, sc)
+    with pytest.raises(ValueError):
+        oracle.pssm_scores(32, 5, -4, 4)
+
+
+def brute_map_pssm(genome: str, F: int, read: str, quals: str, match: int, mismatch: int, scale: int):
+    """Phase one with position-specific scores, by enumeration of every run on every diagonal."""
+    G = len(genome)
+    NF = -(-G // F)
+    Gp = NF * F
+    m = len(read)
+    gpad = genome + "N" * (Gp - G + m)
+    sc = [pssm_py(ord(c), match, mismatch, scale) for c in quals]
+    strands = [(read, sc), (revcomp(read), sc[::-1])]
+    frag = []
+    for f in range(NF):
+        cands = []
+        for sg in range(2):
+            r, p = strands[sg]
+            for d in range(f * F, (f + 1) * F):
+                x = [sub_score(r[k], gpad[d + k], p[k][0], p[k][1]) for k in range(m)]
+                cands.append((brute_mss(x), sg, d))
+        best = max(c[0] for c in cands)
+        first = min((sg, d) for (v, sg, d) in cands if v == best)
+        frag.append((best, first[0], first[1]))
+    order = sorted(range(NF), key=lambda f: (-frag[f][0], f))
+    b1 = order[0]
+    b2 = order[1] if NF > 1 else -1
+    s1 = frag[b1][0]
+    s2 = frag[b2][0] if b2 >= 0 else 0
+    repeat = 1 if (s1 == 0 or 10 * s2 >= 9 * s1) else 0
+    return (b1, b2, s1, s2, frag[b1][2], frag[b1][1], repeat)
+
+
+@pytest.mark.parametrize("F", [1, 4, 9])
+def test_pssm_map_read_bruteforce(F):
+    rng = np.random.default_rng(60 + F)
+    for trial in range(20):
+        G = int(rng.integers(1, 40))
+        m = int(rng.integers(1, 9))
+        genome = "".join(rng.choice(list(ALPHA), p=[.23, .23, .23, .23, .08], size=G))
+        if trial % 3 == 0 and G >= m:
+            s0 = int(rng.integers(0, G - m + 1))
+            read = genome[s0:s0 + m]
+            if trial % 2:
+                read = revcomp(read)
+        else:
+            read = "".join(rng.choice(list(ALPHA), p=[.24, .24, .24, .24, .04], size=m))
+        quals = "".join(chr(33 + int(v)) for v in rng.integers(0, 42, size=m))
+        match, mismatch, scale = [(5, -4, 4), (1, -1, 8), (2, -3, 2)][trial % 3]
+        want = brute_map_pssm(genome, F, read, quals, match, mismatch, scale)
+        got = oracle.map_read(genome, F, read, match, mismatch, quals=quals.encode(), scale=scale)
+        assert got == want, (genome, F, read, quals)
+
+
+def test_pssm_constant_quality_is_the_plain_scan_with_rounded_scores():
+    """With every base at one quality the position-specific scores are constants, so the result
+    is the plain scan's with those two scores."""
+    rng = np.random.default_rng(66)
+    genome = "".join(rng.choice(list("ACGTN"), p=[.24, .24, .24, .24, .04], size=3000))
+    for qc in ("I", "+", "$"):
+        ma, mm = pssm_py(ord(qc), 5, -4, 4)
+        for _ in range(6):
+            m = int(rng.integers(5, 60))
+            s0 = int(rng.integers(0, 3000 - m))
+            read = list(genome[s0:s0 + m].replace("N", "A"))
+            for k in rng.integers(0, m, size=m // 6):
+                read[k] = "ACGT"[(("ACGT".index(read[k])) + 1) % 4]
+            read = "".join(read)
+            got = oracle.map_read(genome, 256, read, 5, -4, quals=(qc * m).encode(), scale=4)
+            want = oracle.map_read(genome, 256, read, ma, mm)
+            assert got == want
+
+
+def test_pssm_nw_bruteforce_tiny():
+    rng = np.random.default_rng(67)
+    for t in range(120):
+        m = int(rng.integers(1, 6))
+        L = int(rng.integers(1, 7))
+        window = "".join(rng.choice(list(ALPHA), p=[.24, .24, .24, .24, .04], size=L))
+        read = "".join(rng.choice(list(ALPHA), p=[.24, .24, .24, .24, .04], size=m))
+        quals = "".join(chr(33 + int(v)) for v in rng.integers(0, 42, size=m))
+        sc = [pssm_py(ord(c), 5, -4, 4) for c in quals]
+        ma, mm = [a for a, _ in sc], [b for _, b in sc]
+        go, ge = [(-40, -4), (-104, -104), (-8, -4)][t % 3]
+        want = brute_glocal(read, window, 0, 0, go, ge, pos=(ma, mm))
+        score, gs, ge_, cig = oracle.nw_banded_pssm(oracle.encode(window), oracle.encode(read), ma, mm, 0, 64, go, ge)
+        assert score == want, (read, window, quals)
+        s2, i, j = alignment_score(read, window[gs:], parse_cigar(cig), 0, 0, go, ge, pos=(ma, mm))
+        assert s2 == score and i == m and gs + j == ge_
