@@ -295,6 +295,31 @@ MSS_API mss_status mss_prop_save(const mss_prop* p, const char* path);
 MSS_API mss_status mss_prop_load(mss_prop* p, const char* path);
 MSS_API int64_t mss_prop_launch_count(const mss_prop* p);
 
+/* ---- Base qualities ("Incorporating base qualities and position specific scoring matrix") ----
+   A base of Phred quality Q (quality character Q + 33, '!'..'~') is right with probability
+   x = 1 - 10^(-Q/10); matching it scores match * x and mismatching it mismatch * x / 3.  The
+   scores are kept in fixed point: times scale (1..32), rounded to the nearest integer with
+   halves away from zero, so results are in units of 1/scale.  A read N, or a genome N, scores
+   the position's mismatch value.  d_quals: one quality character per read base, same offsets
+   as d_reads (device memory).  The reverse strand's base k takes the quality of read base
+   m - 1 - k. */
+/* Phase one with those scores (int16 lanes; read step 1; default scan shape 8 lane pairs x 4
+   query strands, other mss_tune shapes fail with MSS_EINVAL).  Errors as mss_map_reads_device,
+   plus MSS_EINVAL for a null d_quals or a scale outside 1..32, MSS_EOVERFLOW when scale *
+   match > 127, scale * mismatch < -384 (8-bit profile bytes) or max_len * round(scale * match)
+   > 32767; a quality character outside '!'..'~' is reported by mss_sync (MSS_EINVAL). */
+MSS_API mss_status mss_map_reads_quals_device(mss_ctx* ctx, const char* d_reads, const char* d_quals,
+                                              const int64_t* d_offsets, int32_t R, int32_t max_len,
+                                              const mss_score_params* sp, int32_t scale, mss_hit* d_out,
+                                              void* stream);
+/* Phase two with those scores: np->match / np->mismatch are weighted per read base, the gap
+   costs multiplied by scale; the alignment score is in units of 1/scale.  Errors as
+   nw_align_device, plus MSS_EINVAL for a null d_quals or a scale outside 1..32. */
+MSS_API mss_status nw_align_quals_device(mss_ctx* ctx, const char* d_reads, const char* d_quals,
+                                         const int64_t* d_offsets, int32_t R, int32_t max_len, const mss_hit* d_hits,
+                                         const mss_nw_params* np, int32_t scale, mss_aln* d_out, char* d_cigars,
+                                         int32_t cigar_stride, void* stream);
+
 /* ---- SAM output ("Mapping qualities, read lengths, SAM output, and source code") ---- */
 /* MAPQ of a phase-one result: -100 log2(second / best), the paper's probability of a wrong
    mapping being the ratio of the second-best to the best fragment score; rounded to the

@@ -35,7 +35,7 @@ EXPORTS = ("mss_load_genome", "mss_load_genome_device", "mss_get_info", "mss_set
            "mss_prop_get_params", "mss_prop_set_params", "mss_prop_read_codes", "mss_prop_window_codes",
            "mss_prop_embed_device", "mss_prop_grad_device", "mss_prop_train_step", "mss_prop_build_index",
            "mss_map_reads_proposed", "mss_prop_save", "mss_prop_load", "mss_prop_launch_count", "mss_free",
-           "mss_mapq", "mss_format_sam", "mss_last_error")
+           "mss_map_reads_quals_device", "nw_align_quals_device", "mss_mapq", "mss_format_sam", "mss_last_error")
 
 HIT_DTYPE = np.dtype([("best_frag", np.int32), ("second_frag", np.int32), ("best_score", np.int32),
                       ("second_score", np.int32), ("offset", np.int64), ("strand", np.int32), ("flags", np.int32)])
@@ -128,6 +128,8 @@ def load_library(path: str = LIB_PATH):
         "mss_free": ([P], None),
         "mss_last_error": ([], ctypes.c_char_p),
         "mss_mapq": ([i32, i32], i32),
+        "mss_map_reads_quals_device": ([P, P, P, P, i32, i32, P, i32, P, P], i32),
+        "nw_align_quals_device": ([P, P, P, P, i32, i32, P, P, i32, P, P, i32, P], i32),
         "mss_format_sam": ([ctypes.c_char_p, i64, P, P, i32, P, P, P, i32, i32, P, i64], i64),
     }
     for name, (args, res) in sig.items():
@@ -270,6 +272,27 @@ def nw_align(g: Genome, reads, offsets, hits: np.ndarray, match=5, mismatch=-4, 
     _check(st, "nw_align")
     cigars = [bytes(cig[i, :max(out["cigar_len"][i], 0)]).decode() for i in range(R)]
     return out, cigars
+
+
+def mss_map_reads_quals_device(g: Genome, d_reads, d_quals, d_offsets, R: int, max_len: int, match: int,
+                               mismatch: int, scale: int, d_out, stream=None):
+    """Phase one with base qualities (Phred+33, device tensors); d_out: 32*R bytes."""
+    sp = ScoreParams(match, mismatch)
+    _check(load_library().mss_map_reads_quals_device(g.handle, _host_ptr(d_reads), _host_ptr(d_quals),
+                                                     _host_ptr(d_offsets), R, max_len, ctypes.byref(sp), scale,
+                                                     _host_ptr(d_out), _stream_ptr(stream)),
+           "mss_map_reads_quals_device")
+
+
+def nw_align_quals_device(g: Genome, d_reads, d_quals, d_offsets, R: int, max_len: int, d_hits, d_out, d_cigars,
+                          cigar_stride: int, scale: int, match=5, mismatch=-4, gap_open=-26, gap_extend=-26, band=32,
+                          stream=None):
+    npar = NwParams(match, mismatch, gap_open, gap_extend, band, 0)
+    _check(load_library().nw_align_quals_device(g.handle, _host_ptr(d_reads), _host_ptr(d_quals), _host_ptr(d_offsets),
+                                                R, max_len, _host_ptr(d_hits), ctypes.byref(npar), scale,
+                                                _host_ptr(d_out), _host_ptr(d_cigars), cigar_stride,
+                                                _stream_ptr(stream)),
+           "nw_align_quals_device")
 
 
 def mss_mapq(best_score: int, second_score: int) -> int:

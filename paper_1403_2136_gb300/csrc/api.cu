@@ -2,6 +2,7 @@
 // Every compute step runs in the kernels of pack.cu, scan.cu and nw.cu; this file only
 // checks arguments, sizes buffers and enqueues work.
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -74,6 +75,9 @@ struct GraphKey {
   int64_t chunk_len;
   cudaStream_t stream;
   const void* ws[4];  // workspace pointers baked into the graph
+  const void* quals;  // base qualities of the call (null: plain scores)
+  const void* qtab;
+  int32_t scale;
   bool timing;        // event nodes around the scan
   bool operator==(const GraphKey& o) const { return memcmp(this, &o, sizeof(GraphKey)) == 0; }
 };
@@ -90,6 +94,12 @@ struct mss_ctx {
   int64_t launches = 0;
   mss_tune tune{-1, 0, 0, 0, 0, 0};  // automatic
   int32_t read_step = 1;              // 2: "MaxSSmap_fast" (every other read base)
+  // position-specific scores from base qualities: the qualities and fixed-point scale of the
+  // mapping call in progress (null between calls), and the device tables of phase one / two
+  const char* call_quals = nullptr;
+  int32_t call_scale = 0;
+  DevBuf qtab_scan, qtab_nw;
+  int32_t qtab_scan_key[3] = {0, 0, 0}, qtab_nw_key[3] = {0, 0, 0};
   DevBuf hist, order, partial, queue, nw_scratch;
   DevBuf h_reads, h_offsets, h_hits, h_alns, h_cigars;  // staging for the host-pointer calls
   cudaGraphExec_t graph = nullptr;
@@ -165,25 +175,30 @@ mss_status read_err(mss_ctx* c, cudaStream_t s) {
   if (h & ERR_BAD_LEN) return fail(MSS_EREADLEN, "read length 0 or above the declared maximum");
   if (h & ERR_TIMEOUT) return fail(MSS_ETIMEOUT, "a bounded device wait gave up");
   if (h & ERR_SELFCHECK) return fail(MSS_ESTATE, "best-fragment rescan disagreed with the scan");
+  if (h & ERR_BAD_QUAL) return fail(MSS_EINVAL, "base quality character outside '!'..'~'");
   return MSS_OK;
 }
 
 mss_status resolve_config(const mss_ctx* c, int32_t max_len, const mss_score_params* sp, ScanConfig* cfg,
                           int* grid, int64_t* chunk_len, int32_t R, int32_t* n_chunks, size_t* smem, int* slots) {
   const mss_tune& t = c->tune;
-  bool exact16 = f16_path_exact(max_len, sp->match, sp->mismatch);
+  const bool pssm = c->call_quals != nullptr;
+  bool exact16 = !pssm && f16_path_exact(max_len, sp->match, sp->mismatch);
   int variant = t.variant;
   if (variant < 0) variant = exact16 ? 1 : 0;
   if (variant == 1 && !exact16)
-    return fail(MSS_EINVAL, "f16 scan variant is not exact for these scores / read lengths");
+    return fail(MSS_EINVAL, "f16 scan variant is not exact for these scores / read lengths (or base qualities)");
   cfg->variant = variant;
   cfg->pairs = t.pairs ? t.pairs : 8;
   cfg->queries = t.queries ? t.queries : (cfg->pairs == 8 ? 4 : 8);
   cfg->threads = 256;
   cfg->max_len = max_len;
   cfg->step = c->read_step;
+  cfg->pssm = pssm;
   if (cfg->step == 2 && (cfg->pairs != 8 || cfg->queries != 4))
     return fail(MSS_EINVAL, "read step 2 is built for 8 lane pairs x 4 query strands only");
+  if (pssm && (cfg->pairs != 8 || cfg->queries != 4 || cfg->step != 1))
+    return fail(MSS_EINVAL, "base qualities are built for read step 1 and 8 lane pairs x 4 query strands only");
   *slots = scan_ring_slots(*cfg, c->F);
   *smem = scan_smem_bytes(*cfg, max_len, *slots);
   if (*smem == 0)
@@ -253,6 +268,8 @@ mss_status enqueue_map(mss_ctx* c, const char* d_reads, const int64_t* d_offsets
     a.prof_mismatch = (uint32_t)sp->mismatch & 0xFFu;
     a.mm_word = a.prof_mismatch * 0x01010101u;
   }
+  a.quals = c->call_quals;
+  a.qtab = c->call_quals ? (const int16_t*)c->qtab_scan.p : nullptr;
   const int g = (int)std::max<int64_t>(1, std::min<int64_t>(grid, a.n_items));
   // inside a stream capture the events become external event nodes of the graph; outside one
   // they are recorded plainly
@@ -281,6 +298,8 @@ mss_status enqueue_map(mss_ctx* c, const char* d_reads, const int64_t* d_offsets
   f.match = sp->match;
   f.mismatch = sp->mismatch;
   f.step = cfg.step;
+  f.quals = a.quals;
+  f.qtab = a.qtab;
   f.hits = d_out;
   f.err = c->d_err;
   CK(launch_finalize(f, s), "finalize kernel");
@@ -330,6 +349,9 @@ mss_status map_device(mss_ctx* c, const char* d_reads, const int64_t* d_offsets,
   key.ws[1] = c->order.p;
   key.ws[2] = c->partial.p;
   key.ws[3] = c->queue.p;
+  key.quals = c->call_quals;
+  key.qtab = c->call_quals ? c->qtab_scan.p : nullptr;
+  key.scale = c->call_quals ? c->call_scale : 0;
   key.timing = c->timing;
   if (!(c->have_graph && c->gkey == key)) {
     if (c->graph) {
@@ -374,7 +396,7 @@ mss_status check_nw(const mss_nw_params* np, int32_t cigar_stride) {
 
 mss_status nw_device(mss_ctx* c, const char* d_reads, const int64_t* d_offsets, int32_t R, int32_t max_len,
                      const mss_hit* d_hits, const mss_nw_params* np, mss_aln* d_out, char* d_cig, int32_t stride,
-                     cudaStream_t s) {
+                     cudaStream_t s, const char* d_quals = nullptr, int32_t scale = 1) {
   mss_status st = check_nw(np, stride);
   if (st) return st;
   if (R < 0) return fail(MSS_EINVAL, "R < 0");
@@ -395,9 +417,11 @@ mss_status nw_device(mss_ctx* c, const char* d_reads, const int64_t* d_offsets, 
   a.hits = d_hits;
   a.match = np->match;
   a.mismatch = np->mismatch;
-  a.gap_open = np->gap_open;
-  a.gap_extend = np->gap_extend;
+  a.gap_open = np->gap_open * (d_quals ? scale : 1);   // gaps in the fixed point of the table
+  a.gap_extend = np->gap_extend * (d_quals ? scale : 1);
   a.band = np->band;
+  a.quals = d_quals;
+  a.qtab = d_quals ? (const int16_t*)c->qtab_nw.p : nullptr;
   a.alns = d_out;
   a.cigars = d_cig;
   a.cigar_stride = stride;
@@ -560,6 +584,70 @@ mss_status mss_get_tune(const mss_ctx* c, mss_tune* t) {
   if (check_ctx(c) || !t) return fail(MSS_EINVAL, "null argument");
   *t = c->tune;
   return MSS_OK;
+}
+
+namespace {
+
+// Position-specific scores of base qualities ("Incorporating base qualities and position
+// specific scoring matrix"): a base of Phred quality Q is right with probability
+// x = 1 - 10^(-Q/10); a match scores match * x, a mismatch mismatch * x / 3; both in fixed point
+// (times scale), rounded to the nearest integer with halves away from zero.
+void pssm_table(int32_t match, int32_t mismatch, int32_t scale, int16_t* tab) {
+  for (int Q = 0; Q < kQualLevels; ++Q) {
+    const double x = 1.0 - pow(10.0, -Q / 10.0);
+    tab[2 * Q] = (int16_t)lround((double)scale * match * x);
+    tab[2 * Q + 1] = (int16_t)lround((double)scale * mismatch * x / 3.0);
+  }
+}
+
+mss_status ensure_qtab(DevBuf& buf, int32_t* key, int32_t match, int32_t mismatch, int32_t scale) {
+  if (buf.p && key[0] == match && key[1] == mismatch && key[2] == scale) return MSS_OK;
+  int16_t tab[2 * kQualLevels];
+  pssm_table(match, mismatch, scale, tab);
+  CK(buf.ensure(sizeof(tab)), "quality table");
+  CK(cudaMemcpy(buf.p, tab, sizeof(tab), cudaMemcpyHostToDevice), "quality table upload");
+  key[0] = match;
+  key[1] = mismatch;
+  key[2] = scale;
+  return MSS_OK;
+}
+
+}  // namespace
+
+mss_status mss_map_reads_quals_device(mss_ctx* c, const char* d_reads, const char* d_quals, const int64_t* d_offsets,
+                                      int32_t R, int32_t max_len, const mss_score_params* sp, int32_t scale,
+                                      mss_hit* d_out, void* stream) {
+  if (check_ctx(c)) return MSS_EINVAL;
+  mss_status st = check_scores(c, max_len, sp);
+  if (st) return st;
+  if (!d_quals) return fail(MSS_EINVAL, "null base qualities");
+  if (scale < 1 || scale > 32) return fail(MSS_EINVAL, "scale %d outside [1, 32]", scale);
+  if ((int64_t)scale * sp->match > 127 || (int64_t)scale * sp->mismatch < -3 * 128)
+    return fail(MSS_EOVERFLOW, "scale * match above 127 or scale * mismatch / 3 below -128 (8-bit profile bytes)");
+  if ((int64_t)max_len * (int64_t)lround((double)scale * sp->match) > 32767)
+    return fail(MSS_EOVERFLOW, "max_len * scale * match exceeds the 16-bit lanes");
+  st = ensure_qtab(c->qtab_scan, c->qtab_scan_key, sp->match, sp->mismatch, scale);
+  if (st) return st;
+  c->call_quals = d_quals;
+  c->call_scale = scale;
+  st = map_device(c, d_reads, d_offsets, R, max_len, sp, d_out, (cudaStream_t)stream, true);
+  c->call_quals = nullptr;
+  c->call_scale = 0;
+  return st;
+}
+
+mss_status nw_align_quals_device(mss_ctx* c, const char* d_reads, const char* d_quals, const int64_t* d_offsets,
+                                 int32_t R, int32_t max_len, const mss_hit* d_hits, const mss_nw_params* np,
+                                 int32_t scale, mss_aln* d_out, char* d_cig, int32_t stride, void* stream) {
+  if (check_ctx(c)) return MSS_EINVAL;
+  mss_status st = check_nw(np, stride);
+  if (st) return st;
+  if (!d_quals) return fail(MSS_EINVAL, "null base qualities");
+  if (scale < 1 || scale > 32) return fail(MSS_EINVAL, "scale %d outside [1, 32]", scale);
+  st = ensure_qtab(c->qtab_nw, c->qtab_nw_key, np->match, np->mismatch, scale);
+  if (st) return st;
+  return nw_device(c, d_reads, d_offsets, R, max_len, d_hits, np, d_out, d_cig, stride, (cudaStream_t)stream, d_quals,
+                   scale);
 }
 
 mss_status mss_map_reads_device(mss_ctx* c, const char* d_reads, const int64_t* d_offsets, int32_t R,

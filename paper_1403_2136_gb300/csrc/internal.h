@@ -11,7 +11,11 @@ enum : int32_t {
   ERR_BAD_LEN = 2,      // a read of length 0 or above the declared maximum
   ERR_TIMEOUT = 4,      // a bounded mbarrier wait gave up
   ERR_SELFCHECK = 8,    // the best-fragment rescan disagreed with the scan
+  ERR_BAD_QUAL = 16,    // a base-quality character outside '!'..'~'
 };
+// Position-specific scores of base qualities: entry 2Q, 2Q + 1 = (match, mismatch) of a base of
+// Phred quality Q = 0..93, in fixed point (built on the host, see pssm_table in api.cu).
+constexpr int kQualLevels = 94;
 
 // Genome tiles: the largest tile a scan variant uses and the extra positions past the last
 // fragment that a tile may read; the packed genome is allocated (zero = N) to cover them.
@@ -41,6 +45,7 @@ struct ScanConfig {
   int threads;  // NT
   int max_len;  // longest read of the call (selects the selector-row size)
   int step;     // read step: 1 every base, 2 every other base ("MaxSSmap_fast")
+  bool pssm;    // position-specific scores from base qualities (int16 lanes only)
 };
 
 struct ScanArgs {
@@ -64,6 +69,8 @@ struct ScanArgs {
   uint32_t prof_match;     // byte encodings used to build the query profile
   uint32_t prof_mismatch;
   uint32_t mm_word;        // second PRMT operand (genome N -> mismatch)
+  const char* quals;       // base qualities (Phred+33, same offsets as the reads) or null
+  const int16_t* qtab;     // [kQualLevels][2] position-specific scores when quals is set
 };
 
 // Smallest tile (diagonals) of a configuration; chunk lengths are multiples of it.
@@ -88,6 +95,8 @@ struct FinalArgs {
   const int4* partial;
   int32_t match, mismatch;
   int32_t step;  // read step of the scan (the rescan samples the read the same way)
+  const char* quals;    // base qualities or null (as ScanArgs)
+  const int16_t* qtab;
   void* hits;  // mss_hit[R], input order
   int32_t* err;
 };
@@ -103,6 +112,8 @@ struct NwArgs {
   int32_t max_len;
   const void* hits;  // mss_hit[R]
   int32_t match, mismatch, gap_open, gap_extend, band;
+  const char* quals;     // base qualities or null: per read base (match, mismatch) from qtab
+  const int16_t* qtab;
   void* alns;        // mss_aln[R]
   char* cigars;
   int32_t cigar_stride;

@@ -35,7 +35,12 @@ int64_t nw_scratch_per_warp(int32_t max_len, int32_t band) {
 __global__ void __launch_bounds__(kNwWarps * 32) k_nw(NwArgs a) {
   __shared__ uint8_t s_q[kNwWarps][MSS_MAX_READ_LEN];
   __shared__ uint8_t s_w[kNwWarps][MSS_MAX_READ_LEN + 2 * 64 + 16];
+  __shared__ uint8_t s_qual[kNwWarps][MSS_MAX_READ_LEN];  // Phred values in strand order (quals only)
+  __shared__ int16_t s_tab[kQualLevels][2];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  if (a.quals)
+    for (int e = threadIdx.x; e < 2 * kQualLevels; e += blockDim.x) s_tab[e >> 1][e & 1] = a.qtab[e];
+  __syncthreads();
   const int gw = blockIdx.x * kNwWarps + wib;
   if (gw >= a.n_warps) return;
   uint8_t* tb = a.scratch + (int64_t)gw * a.scratch_per_warp;
@@ -71,6 +76,14 @@ __global__ void __launch_bounds__(kNwWarps * 32) k_nw(NwArgs a) {
         if (cf > 4) cf = 4;
       }
       s_q[wib][k] = (uint8_t)cf;
+      if (a.quals) {
+        int Q = (int)(uint8_t)a.quals[off + (hit.strand ? m - 1 - k : k)] - 33;
+        if (Q < 0 || Q >= kQualLevels) {
+          atomicOr(a.err, ERR_BAD_QUAL);
+          Q = 0;
+        }
+        s_qual[wib][k] = (uint8_t)Q;
+      }
     }
     for (int j = lane; j < L; j += 32) s_w[wib][j] = (uint8_t)genome_code(a.g2, a.gm, ws + j);
     __syncwarp();
@@ -87,6 +100,12 @@ __global__ void __launch_bounds__(kNwWarps * 32) k_nw(NwArgs a) {
     }
     for (int32_t i = 1; i <= m; ++i) {
       const uint32_t qc = s_q[wib][i - 1];
+      int32_t row_match = a.match, row_mismatch = a.mismatch;
+      if (a.quals) {  // position-specific scores of this read base
+        const int Q = s_qual[wib][i - 1];
+        row_match = s_tab[Q][0];
+        row_mismatch = s_tab[Q][1];
+      }
       const int32_t Hn = __shfl_down_sync(0xffffffffu, Hp[0], 1);
       const int32_t Fn = __shfl_down_sync(0xffffffffu, Fp[0], 1);
       int32_t Hd[kNwCells], Fc[kNwCells], Dg[kNwCells], Hup[kNwCells];
@@ -101,7 +120,7 @@ __global__ void __launch_bounds__(kNwWarps * 32) k_nw(NwArgs a) {
         int32_t dg = kNeg;
         if (valid[c] && j >= 1 && Hp[c] > kNeg / 2) {
           const uint32_t gc = s_w[wib][j - 1];
-          dg = Hp[c] + ((qc < 4 && qc == gc) ? a.match : a.mismatch);
+          dg = Hp[c] + ((qc < 4 && qc == gc) ? row_match : row_mismatch);
         }
         const int32_t f = clampneg(max(hu + go, fu + ge));
         Hup[c] = hu;

@@ -47,16 +47,19 @@ struct ScanGeo {
 };
 
 struct SmemLayout {
-  size_t prof, sel, raw, ring, top, mbar, misc, total;
+  size_t prof, profn, sel, raw, ring, top, mbar, misc, total;
 };
 
+// pssm: a second profile array holds, per read position and query, the word a genome N
+// selects (the position's mismatch score)
 template <int D, int RQ, int NT, int MAXL>
-__host__ __device__ inline SmemLayout scan_layout(int32_t max_len, int32_t ring_slots) {
+__host__ __device__ inline SmemLayout scan_layout(int32_t max_len, int32_t ring_slots, bool pssm) {
   using Geo = ScanGeo<D, NT, MAXL>;
   SmemLayout L;
   size_t mpad_max = (size_t)((max_len + 7) & ~7);
   L.prof = 0;
-  L.sel = L.prof + (mpad_max + 1) * RQ * 4;  // one padding row: the scan reads one row ahead
+  L.profn = L.prof + (mpad_max + 1) * RQ * 4;  // one padding row: the scan reads one row ahead
+  L.sel = L.profn + (pssm ? (mpad_max + 1) * RQ * 4 : 0);
   L.raw = L.sel + 2 * (size_t)Geo::kSelWords * 4;  // two selector buffers (tile t and t+1)
   L.raw = (L.raw + 127) & ~(size_t)127;
   L.ring = L.raw + 2 * (size_t)Geo::kRawBytes;
@@ -70,7 +73,10 @@ __host__ __device__ inline SmemLayout scan_layout(int32_t max_len, int32_t ring_
 
 // STEP = 1: every read base; STEP = 2: every other read base ("MaxSSmap_fast"), so step k of
 // diagonal d compares read base STEP*k with genome base d + STEP*k.
-template <bool F16, int D, int RQ, int NT, int MAXL, int MINB, int STEP>
+// PSSM: position-specific scores from base qualities ("Incorporating base qualities and
+// position specific scoring matrix"), int16 lanes only: the profile bytes and the genome-N word
+// come from the read position's quality.
+template <bool F16, int D, int RQ, int NT, int MAXL, int MINB, int STEP, bool PSSM>
 __global__ void __launch_bounds__(NT, MINB) k_scan(ScanArgs a) {
   using Geo = ScanGeo<D, NT, MAXL>;
   constexpr int RG = RQ / 2;
@@ -81,11 +87,13 @@ __global__ void __launch_bounds__(NT, MINB) k_scan(ScanArgs a) {
   static_assert(RQ % 4 == 0, "profile rows are read as uint4");
   static_assert(STEP == 1 || STEP == 2, "read step 1 or 2");
   static_assert(BS % 2 == 0, "the running max is updated every second step");
+  static_assert(!(PSSM && F16), "position-specific scores run on the int16 lanes");
   static_assert(RG <= 4, "read lengths occupy 16 bytes of the misc area");
 
   extern __shared__ __align__(128) uint8_t smem[];
-  const SmemLayout L = scan_layout<D, RQ, NT, MAXL>(a.max_len, a.ring_slots);
+  const SmemLayout L = scan_layout<D, RQ, NT, MAXL>(a.max_len, a.ring_slots, PSSM);
   uint32_t* prof = reinterpret_cast<uint32_t*>(smem + L.prof);
+  uint32_t* profn = reinterpret_cast<uint32_t*>(smem + L.profn);
   uint32_t* const sel_base = reinterpret_cast<uint32_t*>(smem + L.sel);
   uint8_t* raw = smem + L.raw;
   int32_t* ring = reinterpret_cast<int32_t*>(smem + L.ring);
@@ -148,8 +156,18 @@ __global__ void __launch_bounds__(NT, MINB) k_scan(ScanArgs a) {
       const int len = s_len[r];
       const int kr = STEP * k;
       uint32_t code = 4;
+      uint32_t pma = a.prof_match, pmm = a.prof_mismatch;
       if (kr < len) {
         const int64_t pos = s_off[r] + ((q & 1) ? (len - 1 - kr) : kr);
+        if (PSSM) {  // the base's own quality (the reverse strand's base k is read base len-1-k)
+          int Q = (int)(uint8_t)a.quals[pos] - 33;
+          if (Q < 0 || Q >= kQualLevels) {
+            atomicOr(a.err, ERR_BAD_QUAL);
+            Q = 0;
+          }
+          pma = (uint32_t)a.qtab[2 * Q] & 0xFFu;
+          pmm = (uint32_t)a.qtab[2 * Q + 1] & 0xFFu;
+        }
         code = ascii_code((uint8_t)a.reads[pos]);
         if (code == 5) {
           atomicOr(a.err, ERR_BAD_CHAR);
@@ -157,7 +175,8 @@ __global__ void __launch_bounds__(NT, MINB) k_scan(ScanArgs a) {
         }
         if ((q & 1) && code < 4) code = 3 - code;
       }
-      prof[e] = profile_word(code, a.prof_match, a.prof_mismatch);
+      prof[e] = profile_word(code, pma, pmm);
+      if (PSSM) profn[e] = pmm * 0x01010101u;
     }
 
     const int64_t c0 = (int64_t)c * a.chunk_len;
@@ -257,9 +276,12 @@ __global__ void __launch_bounds__(NT, MINB) k_scan(ScanArgs a) {
 
       // profile row of the next step, loaded one step ahead (hides the shared-memory latency,
       // also across block boundaries; the row after the last is padding)
-      uint4 pnext[RQ / 4];
+      uint4 pnext[RQ / 4], nnext[RQ / 4];
 #pragma unroll
-      for (int v = 0; v < RQ / 4; ++v) pnext[v] = reinterpret_cast<const uint4*>(prof)[v];
+      for (int v = 0; v < RQ / 4; ++v) {
+        pnext[v] = reinterpret_cast<const uint4*>(prof)[v];
+        if (PSSM) nnext[v] = reinterpret_cast<const uint4*>(profn)[v];
+      }
 
       for (int k0 = 0; k0 < mpad; k0 += BS) {
         // positions entering the window during this block: p = tid*SPAN + STEP*k0 + D + i,
@@ -269,23 +291,33 @@ __global__ void __launch_bounds__(NT, MINB) k_scan(ScanArgs a) {
         const int kk = STEP * k0 + D;
         const uint32_t* sp = sel + (kk % SPAN) * W + tid + kk / SPAN;
         const uint4* pp = reinterpret_cast<const uint4*>(prof + (k0 + 1) * RQ);
+        const uint4* pn = reinterpret_cast<const uint4*>(profn + (k0 + 1) * RQ);
 #pragma unroll
         for (int u = 0; u < BS; ++u) {
-          uint32_t pw[RQ];
+          uint32_t pw[RQ], nw[RQ];
 #pragma unroll
           for (int v = 0; v < RQ / 4; ++v) {
             pw[4 * v + 0] = pnext[v].x;
             pw[4 * v + 1] = pnext[v].y;
             pw[4 * v + 2] = pnext[v].z;
             pw[4 * v + 3] = pnext[v].w;
+            if (PSSM) {
+              nw[4 * v + 0] = nnext[v].x;
+              nw[4 * v + 1] = nnext[v].y;
+              nw[4 * v + 2] = nnext[v].z;
+              nw[4 * v + 3] = nnext[v].w;
+            }
           }
 #pragma unroll
-          for (int v = 0; v < RQ / 4; ++v) pnext[v] = pp[u * (RQ / 4) + v];
+          for (int v = 0; v < RQ / 4; ++v) {
+            pnext[v] = pp[u * (RQ / 4) + v];
+            if (PSSM) nnext[v] = pn[u * (RQ / 4) + v];
+          }
 #pragma unroll
           for (int q = 0; q < RQ; ++q) {
 #pragma unroll
             for (int j = 0; j < D; ++j) {
-              const uint32_t s = prmt(pw[q], mmw, win[(j + STEP * u) % D]);
+              const uint32_t s = prmt(pw[q], PSSM ? nw[q] : mmw, win[(j + STEP * u) % D]);
               const uint32_t h = kadane_step<F16>(H[q][j], s);
               if ((u & 1) != (j & 1)) M[q][j] = __vimax3_s16x2(M[q][j], H[q][j], h);
               H[q][j] = h;
@@ -364,39 +396,41 @@ __global__ void __launch_bounds__(NT, MINB) k_scan(ScanArgs a) {
 }
 
 // ---------------------------------------------------------------- host side of the scan
-// (f16, D, RQ, NT, MAXL, min CTAs per SM, read step)
-#define MSS_SCAN_VARIANTS(X)        \
-  X(false, 4, 8, 256, 512, 2, 1)    \
-  X(true, 4, 8, 256, 512, 2, 1)     \
-  X(false, 8, 4, 256, 512, 2, 1)    \
-  X(true, 8, 4, 256, 512, 2, 1)     \
-  X(false, 4, 4, 256, 512, 2, 1)    \
-  X(true, 4, 4, 256, 512, 2, 1)     \
-  X(false, 4, 8, 256, 2432, 2, 1)   \
-  X(true, 4, 8, 256, 2432, 2, 1)    \
-  X(false, 8, 4, 256, 2432, 2, 1)   \
-  X(true, 8, 4, 256, 2432, 2, 1)    \
-  X(false, 4, 4, 256, 2432, 2, 1)   \
-  X(true, 4, 4, 256, 2432, 2, 1)    \
-  X(false, 8, 4, 256, 512, 2, 2)    \
-  X(true, 8, 4, 256, 512, 2, 2)     \
-  X(false, 8, 4, 256, 2432, 2, 2)   \
-  X(true, 8, 4, 256, 2432, 2, 2)
+// (f16, D, RQ, NT, MAXL, min CTAs per SM, read step, position-specific scores)
+#define MSS_SCAN_VARIANTS(X)               \
+  X(false, 4, 8, 256, 512, 2, 1, false)    \
+  X(true, 4, 8, 256, 512, 2, 1, false)     \
+  X(false, 8, 4, 256, 512, 2, 1, false)    \
+  X(true, 8, 4, 256, 512, 2, 1, false)     \
+  X(false, 4, 4, 256, 512, 2, 1, false)    \
+  X(true, 4, 4, 256, 512, 2, 1, false)     \
+  X(false, 4, 8, 256, 2432, 2, 1, false)   \
+  X(true, 4, 8, 256, 2432, 2, 1, false)    \
+  X(false, 8, 4, 256, 2432, 2, 1, false)   \
+  X(true, 8, 4, 256, 2432, 2, 1, false)    \
+  X(false, 4, 4, 256, 2432, 2, 1, false)   \
+  X(true, 4, 4, 256, 2432, 2, 1, false)    \
+  X(false, 8, 4, 256, 512, 2, 2, false)    \
+  X(true, 8, 4, 256, 512, 2, 2, false)     \
+  X(false, 8, 4, 256, 2432, 2, 2, false)   \
+  X(true, 8, 4, 256, 2432, 2, 2, false)    \
+  X(false, 8, 4, 256, 512, 2, 1, true)     \
+  X(false, 8, 4, 256, 2432, 2, 1, true)
 
 // reads up to 512 bases use selector rows sized for 512 (less shared memory per CTA)
 static int maxl_of(int32_t max_len) { return max_len <= 512 ? 512 : 2432; }
 
-template <bool F16, int D, int RQ, int NT, int MAXL, int MINB, int STEP>
+template <bool F16, int D, int RQ, int NT, int MAXL, int MINB, int STEP, bool PSSM>
 static const void* scan_fn() {
-  return reinterpret_cast<const void*>(&k_scan<F16, D, RQ, NT, MAXL, MINB, STEP>);
+  return reinterpret_cast<const void*>(&k_scan<F16, D, RQ, NT, MAXL, MINB, STEP, PSSM>);
 }
 
 static const void* pick_scan(const ScanConfig& c) {
   const int ml = maxl_of(c.max_len);
-#define X(f, d, rq, nt, mx, mb, st)                                                                \
+#define X(f, d, rq, nt, mx, mb, st, ps)                                                            \
   if (c.variant == (f ? 1 : 0) && c.pairs == d && c.queries == rq && c.threads == nt && ml == mx && \
-      c.step == st)                                                                                \
-    return scan_fn<f, d, rq, nt, mx, mb, st>();
+      c.step == st && c.pssm == ps)                                                                \
+    return scan_fn<f, d, rq, nt, mx, mb, st, ps>();
   MSS_SCAN_VARIANTS(X)
 #undef X
   return nullptr;
@@ -408,9 +442,9 @@ int64_t scan_tile_diags(const ScanConfig& c) { return (int64_t)c.threads * 2 * c
 
 size_t scan_smem_bytes(const ScanConfig& c, int32_t max_len, int32_t ring_slots) {
   const int ml = maxl_of(max_len);
-#define X(f, d, rq, nt, mx, mb, st)                                                \
+#define X(f, d, rq, nt, mx, mb, st, ps)                                            \
   if (c.pairs == d && c.queries == rq && c.threads == nt && ml == mx)              \
-    return scan_layout<d, rq, nt, mx>(max_len, ring_slots).total;
+    return scan_layout<d, rq, nt, mx>(max_len, ring_slots, c.pssm).total;
   MSS_SCAN_VARIANTS(X)
 #undef X
   return 0;
@@ -450,7 +484,12 @@ constexpr int kFinChunk = 1024;  // diagonals staged per pass
 __global__ void __launch_bounds__(kFinWarps * 32) k_finalize(FinalArgs a) {
   __shared__ uint8_t s_gen[kFinWarps][kFinChunk + MSS_MAX_READ_LEN + 16];
   __shared__ uint8_t s_q[kFinWarps][2][MSS_MAX_READ_LEN];
+  __shared__ uint8_t s_qual[kFinWarps][MSS_MAX_READ_LEN];  // Phred values, read order (quals only)
+  __shared__ int8_t s_tab[kQualLevels][2];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  if (a.quals)
+    for (int e = threadIdx.x; e < 2 * kQualLevels; e += blockDim.x) s_tab[e >> 1][e & 1] = (int8_t)a.qtab[e];
+  __syncthreads();
   const int p = blockIdx.x * kFinWarps + wib;
   if (p >= a.R) return;
   const int ridx = a.order[p];
@@ -471,6 +510,10 @@ __global__ void __launch_bounds__(kFinWarps * 32) k_finalize(FinalArgs a) {
     if (cf > 4) cf = 4;
     s_q[wib][0][k] = (uint8_t)cf;
     s_q[wib][1][m - 1 - k] = (uint8_t)(cf < 4 ? 3 - cf : 4);
+    if (a.quals) {
+      int Q = (int)(uint8_t)a.quals[off + k] - 33;
+      s_qual[wib][k] = (uint8_t)(Q < 0 || Q >= kQualLevels ? 0 : Q);
+    }
   }
   __syncwarp();
 
@@ -486,11 +529,21 @@ __global__ void __launch_bounds__(kFinWarps * 32) k_finalize(FinalArgs a) {
       __syncwarp();
       for (int64_t i = lane; i < nd; i += 32) {
         int32_t h = 0, mx = 0;
-        for (int k = 0; k < m; k += a.step) {
-          const uint32_t qc = s_q[wib][sg][k], gc = s_gen[wib][i + k];
-          h += (qc < 4 && qc == gc) ? a.match : a.mismatch;
-          h = max(h, 0);
-          mx = max(mx, h);
+        if (a.quals) {  // position-specific scores (the reverse strand's base k is read base m-1-k)
+          for (int k = 0; k < m; ++k) {
+            const uint32_t qc = s_q[wib][sg][k], gc = s_gen[wib][i + k];
+            const int Q = s_qual[wib][sg ? m - 1 - k : k];
+            h += (qc < 4 && qc == gc) ? s_tab[Q][0] : s_tab[Q][1];
+            h = max(h, 0);
+            mx = max(mx, h);
+          }
+        } else {
+          for (int k = 0; k < m; k += a.step) {
+            const uint32_t qc = s_q[wib][sg][k], gc = s_gen[wib][i + k];
+            h += (qc < 4 && qc == gc) ? a.match : a.mismatch;
+            h = max(h, 0);
+            mx = max(mx, h);
+          }
         }
         if (mx > bestK) {  // lanes visit (strand, d) in increasing order
           bestK = mx;

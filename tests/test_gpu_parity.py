@@ -293,3 +293,73 @@ def test_fast_step_device_graph_and_back_to_plain(mss):
     with pytest.raises(mss.MssError):
         mss.mss_map_reads(g, reads.seq, reads.offsets, 5, -4)
     g.close()
+
+
+# ---------------------------------------------------------------- base qualities (PSSM)
+def _quals_for(reads_seq, seed):
+    rng = np.random.default_rng(seed)
+    return (33 + rng.integers(2, 42, size=reads_seq.shape[0])).astype(np.uint8)   # Phred 2..41
+
+
+@pytest.mark.parametrize("scale", [4, 1])
+def test_pssm_both_phases_match_oracle(mss, scale):
+    """Position-specific scores from base qualities in phase one and phase two, bit for bit
+    against the oracle (fragments, scores, offsets, strands, flags; NW score, span, CIGAR)."""
+    import torch
+    wl = gen.scaled(gen.workloads()["bact-4.6M"], genome_len=50_000, reads=30)
+    genome, reads = gen.materialize(wl)
+    g_ascii = bytes(genome)
+    strs = [bytes(reads.read(i)) for i in range(reads.count)]
+    strs += [b"A", g_ascii[7000:7150].replace(b"G", b"N", 5), g_ascii[4096 - 50:4096 + 51]]
+    seq, off = concat_reads(strs)
+    quals = _quals_for(seq, 7 + scale)
+    R, ML = len(strs), 150
+    nw = (5, -4, -10, -1, 32)
+    g = mss.mss_load_genome(genome, frag_len=2048, max_read_len=ML)
+    d_seq, d_q, d_off = (torch.from_numpy(x).cuda() for x in (seq, quals, off))
+    d_hits = torch.zeros(R * 32, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.Stream()
+    mss.mss_map_reads_quals_device(g, d_seq, d_q, d_off, R, ML, 5, -4, scale, d_hits, stream=s)
+    mss.mss_sync(g, stream=s)
+    stride = 4 * ML + 64
+    d_alns = torch.zeros(R * 24, dtype=torch.uint8, device="cuda")
+    d_cig = torch.zeros(R * stride, dtype=torch.uint8, device="cuda")
+    mss.nw_align_quals_device(g, d_seq, d_q, d_off, R, ML, d_hits, d_alns, d_cig, stride, scale, *nw, stream=s)
+    mss.mss_sync(g, stream=s)
+    hits = mss.hits_from_bytes(d_hits.cpu())
+    alns = d_alns.cpu().numpy().view(mss.ALN_DTYPE)
+    cig = d_cig.cpu().numpy().reshape(R, stride)
+    cigars = [bytes(cig[i, :max(alns["cigar_len"][i], 0)]).decode() for i in range(R)]
+    oh, oa, oc = oracle.map_batch(genome, 2048, seq, off, 5, -4, nw=nw, quals=quals, scale=scale)
+    assert_hits_equal(hits, oh, f"pssm scale {scale}")
+    assert_alns_equal(alns, cigars, oa, oc, f"pssm scale {scale}")
+    # the graph of the call replays with the same qualities
+    d_hits2 = torch.zeros_like(d_hits)
+    mss.mss_map_reads_quals_device(g, d_seq, d_q, d_off, R, ML, 5, -4, scale, d_hits2, stream=s)
+    mss.mss_sync(g, stream=s)
+    assert torch.equal(d_hits, d_hits2)
+    g.close()
+
+
+def test_pssm_constant_quality_equals_plain_scores_and_errors(mss):
+    """Every base at quality 40 ('I'): phase one equals the plain scan with scores
+    (round(4*5*x), round(4*-4*x/3)) = (20, -5); a bad quality character is reported."""
+    import torch
+    wl = gen.scaled(gen.workloads()["bact-4.6M"], genome_len=40_000, reads=24)
+    genome, reads = gen.materialize(wl)
+    g = mss.mss_load_genome(genome, frag_len=1024, max_read_len=150)
+    R = reads.count
+    d_seq, d_off = torch.from_numpy(reads.seq).cuda(), torch.from_numpy(reads.offsets).cuda()
+    d_q = torch.full((reads.seq.shape[0],), ord("I"), dtype=torch.uint8, device="cuda")
+    d_hits = torch.zeros(R * 32, dtype=torch.uint8, device="cuda")
+    mss.mss_map_reads_quals_device(g, d_seq, d_q, d_off, R, 150, 5, -4, 4, d_hits)
+    mss.mss_sync(g)
+    want = mss.mss_map_reads(g, reads.seq, reads.offsets, 20, -5)
+    assert_hits_equal(mss.hits_from_bytes(d_hits.cpu()), want, "quality 40 = plain 20 / -5")
+    d_q[5] = ord(" ")
+    mss.mss_map_reads_quals_device(g, d_seq, d_q, d_off, R, 150, 5, -4, 4, d_hits)
+    with pytest.raises(mss.MssError):
+        mss.mss_sync(g)
+    with pytest.raises(mss.MssError):
+        mss.mss_map_reads_quals_device(g, d_seq, d_q, d_off, R, 150, 5, -4, 40, d_hits)   # scale above 32
+    g.close()
