@@ -65,6 +65,7 @@ def _lib():
             lib.orc_diag_score_step.restype = i32
             lib.orc_map_read.argtypes = [P, i64, i64, P, i32, i32, i32, ctypes.POINTER(Hit), P]
             lib.orc_map_read_step.argtypes = [P, i64, i64, P, i32, i32, i32, i32, ctypes.POINTER(Hit), P]
+            lib.orc_map_read_excl.argtypes = [P, i64, i64, P, i32, i32, i32, ctypes.POINTER(Hit), P]
             lib.orc_pssm_scores.argtypes = [i32, i32, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
             lib.orc_map_read_pssm.argtypes = [P, i64, i64, P, P, i32, i32, i32, i32, ctypes.POINTER(Hit), P]
             lib.orc_nw_banded_pssm.argtypes = [P, i64, P, P, P, i32, i64, i32, i32, i32, ctypes.POINTER(Aln),
@@ -154,14 +155,18 @@ def nw_banded_pssm(gcodes, qcodes, ma, mm, d: int, W: int, gap_open: int, gap_ex
 
 
 def map_read(genome, F: int, read, match: int, mismatch: int, with_frag_scores: bool = False, step: int = 1,
-             quals=None, scale: int = 4):
+             quals=None, scale: int = 4, exclude_neighbors: bool = False):
     """quals (Phred+33, one per read base): position-specific scores with the given fixed-point scale."""
     g = _buf(genome)
     r = _buf(read)
     h = Hit()
     NF = (g.shape[0] + F - 1) // F
     fs = np.empty(NF, dtype=np.int32) if with_frag_scores else None
-    if quals is not None:
+    if exclude_neighbors:
+        assert quals is None and step == 1
+        rc = _lib().orc_map_read_excl(_p(g), g.shape[0], F, _p(r), r.shape[0], match, mismatch, ctypes.byref(h),
+                                      _p(fs) if fs is not None else None)
+    elif quals is not None:
         qb = _buf(quals)
         assert qb.shape[0] == r.shape[0]
         rc = _lib().orc_map_read_pssm(_p(g), g.shape[0], F, _p(r), _p(qb), r.shape[0], match, mismatch, scale,
@@ -209,7 +214,8 @@ ALN_DTYPE = np.dtype([("score", np.int32), ("cigar_len", np.int32), ("gstart", n
 
 
 def map_batch(genome, F: int, reads: np.ndarray, offsets: np.ndarray, match: int, mismatch: int,
-              nw=None, cigar_cap: int = 1024, step: int = 1, quals=None, scale: int = 4):
+              nw=None, cigar_cap: int = 1024, step: int = 1, quals=None, scale: int = 4,
+              exclude_neighbors: bool = False):
     """Phase one (and phase two when nw = (match, mismatch, open, extend, W)) for a batch.
     Returns (hits structured array, alns structured array or None, list of CIGAR strings or None)."""
     g = _buf(genome)
@@ -220,6 +226,11 @@ def map_batch(genome, F: int, reads: np.ndarray, offsets: np.ndarray, match: int
     alns = np.zeros(R, dtype=ALN_DTYPE) if nw is not None else None
     cig = np.zeros((R, cigar_cap), dtype=np.uint8) if nw is not None else None
     nm, nmm, go, ge, W = nw if nw is not None else (0, 0, 0, 0, 0)
+    if exclude_neighbors:   # phase one only, read by read
+        assert nw is None and quals is None and step == 1
+        for i in range(R):
+            hits[i] = map_read(g, F, rd[off[i]:off[i + 1]], match, mismatch, exclude_neighbors=True)
+        return hits, None, None
     if quals is not None:
         qd = np.ascontiguousarray(quals, dtype=np.uint8)
         assert qd.shape[0] == rd.shape[0]

@@ -93,11 +93,19 @@ int orc_map_read(const char* genome, int64_t G, int64_t F, const char* read, int
 
 static int map_read_impl(const char* genome, int64_t G, int64_t F, const char* read, int32_t m, int32_t match,
                          int32_t mismatch, int32_t step, const int32_t* const* ma, const int32_t* const* mm,
-                         orc_hit* out, int32_t* frag_scores);
+                         int32_t exclude_neighbors, orc_hit* out, int32_t* frag_scores);
 
 int orc_map_read_step(const char* genome, int64_t G, int64_t F, const char* read, int32_t m, int32_t match,
                       int32_t mismatch, int32_t step, orc_hit* out, int32_t* frag_scores) {
-  return map_read_impl(genome, G, F, read, m, match, mismatch, step, 0, 0, out, frag_scores);
+  return map_read_impl(genome, G, F, read, m, match, mismatch, step, 0, 0, 0, out, frag_scores);
+}
+
+/* Top-2 with the neighbours of the best fragment excluded (the paper does not say whether the
+   fragment next to the best may count as the second; this is the alternative reading): the
+   second is the best fragment f with |f - best| > 1. */
+int orc_map_read_excl(const char* genome, int64_t G, int64_t F, const char* read, int32_t m, int32_t match,
+                      int32_t mismatch, orc_hit* out, int32_t* frag_scores) {
+  return map_read_impl(genome, G, F, read, m, match, mismatch, 1, 0, 0, 1, out, frag_scores);
 }
 
 /* "Incorporating base qualities and position specific scoring matrix": a base of Phred
@@ -133,14 +141,14 @@ int orc_map_read_pssm(const char* genome, int64_t G, int64_t F, const char* read
   }
   const int32_t* ma[2] = {maf, mar};
   const int32_t* mm[2] = {mmf, mmr};
-  int rc = map_read_impl(genome, G, F, read, m, match, mismatch, 1, ma, mm, out, frag_scores);
+  int rc = map_read_impl(genome, G, F, read, m, match, mismatch, 1, ma, mm, 0, out, frag_scores);
   free(buf);
   return rc;
 }
 
 static int map_read_impl(const char* genome, int64_t G, int64_t F, const char* read, int32_t m, int32_t match,
                          int32_t mismatch, int32_t step, const int32_t* const* ma, const int32_t* const* mm,
-                         orc_hit* out, int32_t* frag_scores) {
+                         int32_t exclude_neighbors, orc_hit* out, int32_t* frag_scores) {
   if (G <= 0 || F <= 0 || m <= 0 || !out || (step != 1 && step != 2)) return -1;
   int64_t NF = (G + F - 1) / F;
   int64_t Gp = NF * F;
@@ -184,6 +192,7 @@ static int map_read_impl(const char* genome, int64_t G, int64_t F, const char* r
   int64_t b2 = -1;
   for (int64_t f = 0; f < NF; ++f) {
     if (f == b1) continue;
+    if (exclude_neighbors && (f == b1 - 1 || f == b1 + 1)) continue;
     if (b2 < 0 || S[f] > S[b2]) b2 = f;
   }
   out->best_frag = (int32_t)b1;

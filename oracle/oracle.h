@@ -75,6 +75,11 @@ typedef struct {
 int orc_map_read(const char* genome, int64_t G, int64_t F, const char* read, int32_t m, int32_t match,
                  int32_t mismatch, orc_hit* out, int32_t* frag_scores);
 
+/* phase one whose second fragment is the best one not adjacent to the best (|f - best| > 1);
+   second = -1 (score 0) when no such fragment exists */
+int orc_map_read_excl(const char* genome, int64_t G, int64_t F, const char* read, int32_t m, int32_t match,
+                      int32_t mismatch, orc_hit* out, int32_t* frag_scores);
+
 /* phase one with the read sampled every step bases (1 or 2; 2 = "MaxSSmap_fast"), on both
    strands (the reverse strand is sampled after reverse complementing) */
 int orc_map_read_step(const char* genome, int64_t G, int64_t F, const char* read, int32_t m, int32_t match,

@@ -550,3 +550,32 @@ def test_pssm_nw_bruteforce_tiny():
         assert score == want, (read, window, quals)
         s2, i, j = alignment_score(read, window[gs:], parse_cigar(cig), 0, 0, go, ge, pos=(ma, mm))
         assert s2 == score and i == m and gs + j == ge_
+
+
+# ---------------------------------------------------------------- second excluding the best's neighbours
+def test_neighbour_exclusion_bruteforce():
+    """The second is the best fragment f with |f - best| > 1 (ties to the lowest), checked on
+    the brute-force fragment scores; with the neighbours allowed it is the plain second."""
+    rng = np.random.default_rng(70)
+    for trial in range(60):
+        G = int(rng.integers(1, 60))
+        F = int(rng.integers(1, 9))
+        m = int(rng.integers(1, 9))
+        genome = "".join(rng.choice(list(ALPHA), p=[.23, .23, .23, .23, .08], size=G))
+        if trial % 2 == 0 and G >= m:
+            s0 = int(rng.integers(0, G - m + 1))
+            read = genome[s0:s0 + m]
+        else:
+            read = "".join(rng.choice(list(ALPHA), p=[.24, .24, .24, .24, .04], size=m))
+        plain, fs = brute_map(genome, F, read, 2, -3)
+        got = oracle.map_read(genome, F, read, 2, -3, exclude_neighbors=True)
+        b1 = plain[0]
+        others = [f for f in range(len(fs)) if abs(f - b1) > 1]
+        if others:
+            b2 = min(others, key=lambda f: (-fs[f], f))
+            s2 = fs[b2]
+        else:
+            b2, s2 = -1, 0
+        s1 = fs[b1]
+        rep = 1 if (s1 == 0 or 10 * s2 >= 9 * s1) else 0
+        assert got == (b1, b2, s1, s2, plain[4], plain[5], rep), (genome, F, read)
