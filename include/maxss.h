@@ -144,6 +144,13 @@ MSS_API mss_status mss_set_frag_len(mss_ctx* ctx, int64_t frag_len);
    shapes make the mapping calls fail with MSS_EINVAL.  Errors: MSS_EINVAL for a null ctx or
    a step other than 1 or 2. */
 MSS_API mss_status mss_set_read_step(mss_ctx* ctx, int32_t step);
+/* Second-fragment rule ("First phase of MaxSSmap" keeps the second-best fragment to flag
+   repeats; the paper does not say whether the best fragment's neighbours may be that second).
+   0 (default): any fragment other than the best.  1: the best fragment f with |f - best| > 1
+   (-1 and score 0 when none exists); the repeat flag follows the chosen second.  Applies to
+   mss_map_reads*, mss_map_align and mss_map_reads_proposed.  Errors: MSS_EINVAL for a null ctx
+   or a rule other than 0 or 1. */
+MSS_API mss_status mss_set_second_rule(mss_ctx* ctx, int32_t exclude_neighbors);
 MSS_API int32_t mss_get_read_step(const mss_ctx* ctx);  /* -1 for a null ctx */
 MSS_API mss_status mss_set_tune(mss_ctx* ctx, const mss_tune* t);
 MSS_API mss_status mss_get_tune(const mss_ctx* ctx, mss_tune* t);

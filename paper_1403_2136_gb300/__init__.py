@@ -29,6 +29,7 @@ MSS_HIT_REPEAT = 1
 
 # every symbol include/maxss.h declares
 EXPORTS = ("mss_load_genome", "mss_load_genome_device", "mss_get_info", "mss_set_frag_len", "mss_set_read_step",
+           "mss_set_second_rule",
            "mss_get_read_step", "mss_set_tune",
            "mss_get_tune", "mss_map_reads", "mss_map_reads_device", "nw_align", "nw_align_device", "nw_align_device_noalloc", "mss_map_align", "mss_sync",
            "mss_autotune", "mss_scan_timing", "mss_scan_time_ms", "mss_launch_count", "mss_genome_codes", "mss_probe_pipes", "mss_prop_create", "mss_prop_free", "mss_prop_param_count",
@@ -91,6 +92,7 @@ def load_library(path: str = LIB_PATH):
         "mss_get_info": ([P, ctypes.POINTER(GenomeInfo)], i32),
         "mss_set_frag_len": ([P, i64], i32),
         "mss_set_read_step": ([P, i32], i32),
+        "mss_set_second_rule": ([P, i32], i32),
         "mss_get_read_step": ([P], i32),
         "mss_set_tune": ([P, ctypes.POINTER(Tune)], i32),
         "mss_get_tune": ([P, ctypes.POINTER(Tune)], i32),
@@ -215,6 +217,11 @@ def mss_set_frag_len(g: Genome, frag_len: int):
 def mss_set_read_step(g: Genome, step: int):
     """1: every read base; 2: every other read base ("MaxSSmap_fast")."""
     _check(load_library().mss_set_read_step(g.handle, step), "mss_set_read_step")
+
+
+def mss_set_second_rule(g: Genome, exclude_neighbors: bool):
+    """True: the second fragment is the best one not adjacent to the best."""
+    _check(load_library().mss_set_second_rule(g.handle, 1 if exclude_neighbors else 0), "mss_set_second_rule")
 
 
 def mss_get_read_step(g: Genome) -> int:

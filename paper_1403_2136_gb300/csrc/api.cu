@@ -75,6 +75,7 @@ struct GraphKey {
   int64_t chunk_len;
   cudaStream_t stream;
   const void* ws[4];  // workspace pointers baked into the graph
+  int32_t exclude;    // second-fragment rule baked into the finalize node
   const void* quals;  // base qualities of the call (null: plain scores)
   const void* qtab;
   int32_t scale;
@@ -94,6 +95,7 @@ struct mss_ctx {
   int64_t launches = 0;
   mss_tune tune{-1, 0, 0, 0, 0, 0};  // automatic
   int32_t read_step = 1;              // 2: "MaxSSmap_fast" (every other read base)
+  int32_t exclude_neighbors = 0;      // 1: the second fragment is not adjacent to the best
   // position-specific scores from base qualities: the qualities and fixed-point scale of the
   // mapping call in progress (null between calls), and the device tables of phase one / two
   const char* call_quals = nullptr;
@@ -298,6 +300,7 @@ mss_status enqueue_map(mss_ctx* c, const char* d_reads, const int64_t* d_offsets
   f.match = sp->match;
   f.mismatch = sp->mismatch;
   f.step = cfg.step;
+  f.exclude_neighbors = c->exclude_neighbors;
   f.quals = a.quals;
   f.qtab = a.qtab;
   f.hits = d_out;
@@ -325,7 +328,7 @@ mss_status map_device(mss_ctx* c, const char* d_reads, const int64_t* d_offsets,
   const int64_t n_groups = (R + RG - 1) / RG;
   CK(c->hist.ensure(sizeof(int32_t) * (size_t)(max_len + 2)), "workspace");
   CK(c->order.ensure(sizeof(int32_t) * (size_t)R), "workspace");
-  CK(c->partial.ensure(sizeof(int4) * (size_t)(n_groups * RG * n_chunks)), "workspace");
+  CK(c->partial.ensure(2 * sizeof(int4) * (size_t)(n_groups * RG * n_chunks)), "workspace");
   CK(c->queue.ensure(sizeof(int32_t)), "workspace");
 
   if (!use_graph || s == nullptr) {
@@ -349,6 +352,7 @@ mss_status map_device(mss_ctx* c, const char* d_reads, const int64_t* d_offsets,
   key.ws[1] = c->order.p;
   key.ws[2] = c->partial.p;
   key.ws[3] = c->queue.p;
+  key.exclude = c->exclude_neighbors;
   key.quals = c->call_quals;
   key.qtab = c->call_quals ? c->qtab_scan.p : nullptr;
   key.scale = c->call_quals ? c->call_scale : 0;
@@ -488,6 +492,7 @@ bool ctx_view(mss_ctx* c, CtxView* v) {
   v->num_sms = c->num_sms;
   v->d_err = c->d_err;
   v->launches = &c->launches;
+  v->exclude_neighbors = c->exclude_neighbors;
   return true;
 }
 
@@ -562,6 +567,13 @@ mss_status mss_set_read_step(mss_ctx* c, int32_t step) {
 }
 
 int32_t mss_get_read_step(const mss_ctx* c) { return c ? c->read_step : -1; }
+
+mss_status mss_set_second_rule(mss_ctx* c, int32_t exclude_neighbors) {
+  if (check_ctx(c)) return MSS_EINVAL;
+  if (exclude_neighbors != 0 && exclude_neighbors != 1) return fail(MSS_EINVAL, "second rule must be 0 or 1");
+  c->exclude_neighbors = exclude_neighbors;
+  return MSS_OK;
+}
 
 mss_status mss_set_tune(mss_ctx* c, const mss_tune* t) {
   if (check_ctx(c) || !t) return fail(MSS_EINVAL, "null argument");

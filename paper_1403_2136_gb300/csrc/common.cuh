@@ -156,6 +156,68 @@ __device__ __forceinline__ Top2 top2_shfl_xor(Top2 v, int mask) {
 
 __device__ __forceinline__ Top2 top2_empty() { return Top2{-1, 0x7fffffff, -1, 0x7fffffff}; }
 
+// Top-4 over fragments (higher score, then lower fragment), distinct fragments, sorted; empty
+// entries s = -1, f = INT32_MAX.  Enough to find both the best fragment other than the first
+// and the best one not adjacent to it (at most two fragments are adjacent).  Merging lists
+// that share a fragment keeps its larger score, so partial maxima of a fragment split across
+// genome chunks merge exactly: a fragment's true score is the largest of its partial maxima,
+// and in the chunk holding that maximum fewer than four other fragments can precede it.
+struct Top4 {
+  int32_t s[4], f[4];
+};
+
+__device__ __forceinline__ Top4 top4_empty() {
+  Top4 r;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) r.s[i] = -1, r.f[i] = 0x7fffffff;
+  return r;
+}
+
+__device__ __forceinline__ Top4 top4_insert(Top4 a, int32_t s, int32_t f) {
+  bool dup = false;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    if (a.f[i] == f) {
+      dup = true;
+      if (s > a.s[i]) a.s[i] = s;
+    }
+  if (dup) {  // one entry may have grown: bubble it towards the front
+#pragma unroll
+    for (int i = 3; i > 0; --i)
+      if (better(a.s[i], a.f[i], a.s[i - 1], a.f[i - 1])) {
+        const int32_t ts = a.s[i], tf = a.f[i];
+        a.s[i] = a.s[i - 1], a.f[i] = a.f[i - 1];
+        a.s[i - 1] = ts, a.f[i - 1] = tf;
+      }
+    return a;
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)  // carry the new entry down the list; the last one drops out
+    if (better(s, f, a.s[i], a.f[i])) {
+      const int32_t ts = a.s[i], tf = a.f[i];
+      a.s[i] = s, a.f[i] = f;
+      s = ts, f = tf;
+    }
+  return a;
+}
+
+__device__ __forceinline__ Top4 top4_merge(Top4 a, const Top4& b) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    if (b.s[i] >= 0) a = top4_insert(a, b.s[i], b.f[i]);
+  return a;
+}
+
+__device__ __forceinline__ Top4 top4_shfl_xor(const Top4& v, int mask) {
+  Top4 o;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    o.s[i] = __shfl_xor_sync(0xffffffffu, v.s[i], mask);
+    o.f[i] = __shfl_xor_sync(0xffffffffu, v.f[i], mask);
+  }
+  return o;
+}
+
 // ---- packed-lane maximum-scoring-subsequence step (scan and candidate rescoring)
 // PRMT selector for the lane pair (genome code c1 at d + k, code c2 at d + D + k).
 template <bool F16>

@@ -62,7 +62,7 @@ struct ScanArgs {
   int32_t n_items;
   int64_t chunk_len;
   int32_t* queue;
-  int4* partial;
+  int4* partial;           // per (read, chunk): top-4 summary, two int4
   int32_t* err;
   int32_t max_len;
   int32_t ring_slots;
@@ -92,7 +92,8 @@ struct FinalArgs {
   int32_t R;
   int32_t n_chunks;
   int32_t reads_per_group;
-  const int4* partial;
+  const int4* partial;      // per (read, chunk): the top-4 as two int4 (score, fragment) pairs
+  int32_t exclude_neighbors;  // second = best fragment not adjacent to the best
   int32_t match, mismatch;
   int32_t step;  // read step of the scan (the rescan samples the read the same way)
   const char* quals;    // base qualities or null (as ScanArgs)
@@ -145,6 +146,7 @@ struct CtxView {
   int32_t num_sms;
   int32_t* d_err;
   int64_t* launches;
+  int32_t exclude_neighbors;  // second-fragment rule of the context
 };
 bool ctx_view(mss_ctx* c, CtxView* v);
 // Record the thread-local message returned by mss_last_error() and return st.

@@ -71,8 +71,8 @@ cudaError_t prop_score_topk(const void* breads, int32_t R, const void* index, in
 // than max_len set ERR_BAD_LEN in *err and are cut to max_len.
 cudaError_t prop_rescore(const uint32_t* g2, const uint32_t* gm, int64_t F, const char* reads, const int64_t* offsets,
                          const int32_t* idx, int32_t R, int32_t max_len, const int32_t* cand, int32_t K,
-                         int32_t match, int32_t mismatch, void* hits, int32_t* cand_scores, int32_t* err,
-                         int num_sms, cudaStream_t s);
+                         int32_t match, int32_t mismatch, int32_t exclude_neighbors, void* hits,
+                         int32_t* cand_scores, int32_t* err, int num_sms, cudaStream_t s);
 // codes of reads (strand 0 forward, 1 reverse complement) and of genome windows
 cudaError_t prop_read_codes(const char* reads, const int64_t* offsets, const int32_t* idx, const int8_t* strand,
                             int32_t n, int32_t ld, uint8_t* codes, int32_t* lens, cudaStream_t s);

@@ -456,7 +456,8 @@ mss_status mss_map_reads_proposed(mss_ctx* ctx, mss_prop* p, const char* d_reads
   // exact rescoring of the candidates
   PCK(p->cand_x.ensure((size_t)R * K * 4), "candidate maxima");
   PCK(prop_rescore(v.g2, v.gm, p->index_F, d_reads, d_offsets, nullptr, R, max_len, p->cand.as<int32_t>(), K,
-                   sp->match, sp->mismatch, d_out, p->cand_x.as<int32_t>(), v.d_err, v.num_sms, s),
+                   sp->match, sp->mismatch, v.exclude_neighbors, d_out, p->cand_x.as<int32_t>(), v.d_err,
+                   v.num_sms, s),
       "rescore");
   p->launches += 2;
   if (d_cand) PCK(cudaMemcpyAsync(d_cand, p->cand.p, (size_t)R * K * 4, cudaMemcpyDeviceToDevice, s), "cand copy");

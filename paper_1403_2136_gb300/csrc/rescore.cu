@@ -4,7 +4,8 @@
 // scan ("First phase of MaxSSmap"): the maximum, over the diagonals d in [fF, (f+1)F) and
 // both strands, of the maximum-scoring subsequence of the substitution scores along d.  Then
 // the best and second-best fragment among the candidates (higher score, then lower fragment)
-// and the best diagonal/strand inside the best one (+ strand first, then smaller d).
+// and the best diagonal/strand inside the best one (+ strand first, then smaller d); with the
+// neighbour rule of the context the second is the best candidate not adjacent to the best.
 //
 // k_rescore_scan: one CTA per read; the read's two strands sit in a shared-memory profile;
 // each pass covers 2048 diagonals of one candidate (256 threads x 4 packed lane pairs (d,
@@ -185,6 +186,7 @@ struct PickArgs {
   const int32_t* cand_max;
   int32_t K;
   int32_t match, mismatch;
+  int32_t exclude_neighbors;
   void* hits;
 };
 
@@ -199,14 +201,22 @@ __global__ void __launch_bounds__(kPickWarps * 32) k_rescore_pick(PickArgs a) {
   const int64_t l = a.offsets[ridx + 1] - off;
   const int32_t m = l < 0 ? 0 : (l > a.max_len ? a.max_len : (int32_t)l);
 
-  Top2 acc = top2_empty();
+  Top4 t4 = top4_empty();
   for (int c = lane; c < a.K; c += 32) {
     const int32_t f = a.cand[(int64_t)i * a.K + c];
     if (f < 0) continue;
-    acc = top2_merge(acc, Top2{a.cand_max[(int64_t)i * a.K + c], f, -1, 0x7fffffff});
+    t4 = top4_insert(t4, a.cand_max[(int64_t)i * a.K + c], f);
   }
 #pragma unroll
-  for (int s = 16; s > 0; s >>= 1) acc = top2_merge(acc, top2_shfl_xor(acc, s));
+  for (int s = 16; s > 0; s >>= 1) t4 = top4_merge(t4, top4_shfl_xor(t4, s));
+  // the best candidate and the second: the next one, or with the neighbour rule the first one
+  // not adjacent to the best
+  Top2 acc{t4.s[0], t4.f[0], -1, 0x7fffffff};
+#pragma unroll
+  for (int j = 3; j >= 1; --j) {
+    const bool adjacent = t4.f[j] == t4.f[0] - 1 || t4.f[j] == t4.f[0] + 1;
+    if (t4.s[j] >= 0 && !(a.exclude_neighbors && adjacent)) acc.s2 = t4.s[j], acc.f2 = t4.f[j];
+  }
 
   int32_t bestK = -1, bestS = 0;
   int64_t bestD = 0;
@@ -270,8 +280,8 @@ __global__ void __launch_bounds__(kPickWarps * 32) k_rescore_pick(PickArgs a) {
 
 cudaError_t prop_rescore(const uint32_t* g2, const uint32_t* gm, int64_t F, const char* reads, const int64_t* offsets,
                          const int32_t* idx, int32_t R, int32_t max_len, const int32_t* cand, int32_t K,
-                         int32_t match, int32_t mismatch, void* hits, int32_t* cand_scores, int32_t* err,
-                         int num_sms, cudaStream_t s) {
+                         int32_t match, int32_t mismatch, int32_t exclude_neighbors, void* hits,
+                         int32_t* cand_scores, int32_t* err, int num_sms, cudaStream_t s) {
   (void)num_sms;
   if (R <= 0 || K <= 0) return cudaSuccess;
   if (max_len < 1 || max_len > MSS_MAX_READ_LEN || !cand_scores) return cudaErrorInvalidValue;
@@ -321,6 +331,7 @@ cudaError_t prop_rescore(const uint32_t* g2, const uint32_t* gm, int64_t F, cons
   b.K = K;
   b.match = match;
   b.mismatch = mismatch;
+  b.exclude_neighbors = exclude_neighbors;
   b.hits = hits;
   k_rescore_pick<<<(unsigned)((R + kPickWarps - 1) / kPickWarps), kPickWarps * 32, 0, s>>>(b);
   return cudaGetLastError();

@@ -65,7 +65,7 @@ __host__ __device__ inline SmemLayout scan_layout(int32_t max_len, int32_t ring_
   L.ring = L.raw + 2 * (size_t)Geo::kRawBytes;
   L.top = L.ring + (size_t)(RQ / 2) * ring_slots * 4;
   L.top = (L.top + 15) & ~(size_t)15;
-  L.mbar = L.top + (size_t)(RQ / 2) * sizeof(Top2);
+  L.mbar = L.top + (size_t)(RQ / 2) * sizeof(Top4);
   L.misc = L.mbar + 16;                     // item (4 B), read lengths at +16, offsets at +32
   L.total = L.misc + 32 + (size_t)(RQ / 2) * 8;
   return L;
@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(NT, MINB) k_scan(ScanArgs a) {
   uint32_t* const sel_base = reinterpret_cast<uint32_t*>(smem + L.sel);
   uint8_t* raw = smem + L.raw;
   int32_t* ring = reinterpret_cast<int32_t*>(smem + L.ring);
-  Top2* top = reinterpret_cast<Top2*>(smem + L.top);
+  Top4* top = reinterpret_cast<Top4*>(smem + L.top);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L.mbar);
   int32_t* s_item = reinterpret_cast<int32_t*>(smem + L.misc);
   int32_t* s_len = reinterpret_cast<int32_t*>(smem + L.misc + 16);      // [RG]
@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(NT, MINB) k_scan(ScanArgs a) {
       }
       s_len[tid] = len;
       s_off[tid] = off;
-      top[tid] = top2_empty();
+      top[tid] = top4_empty();
     }
     for (int e = tid; e < RG * S; e += NT) ring[e] = 0;
     __syncthreads();
@@ -203,19 +203,19 @@ __global__ void __launch_bounds__(NT, MINB) k_scan(ScanArgs a) {
                   &mbar[buf]);
     };
     auto fold = [&](int r, int32_t lo, int32_t hi) {  // fragments [lo, hi) of read r, one warp
-      Top2 acc = top2_empty();
+      Top4 acc = top4_empty();
       for (int32_t base = lo; base < hi; base += 32) {
         const int32_t f = base + lane;
         if (f < hi) {
           const int slot = r * S + (int)(f % S);
           const int32_t v = ring[slot];
           ring[slot] = 0;
-          acc = top2_merge(acc, Top2{v, f, -1, 0x7fffffff});
+          acc = top4_insert(acc, v, f);
         }
       }
 #pragma unroll
-      for (int m = 16; m > 0; m >>= 1) acc = top2_merge(acc, top2_shfl_xor(acc, m));
-      if (lane == 0) top[r] = top2_merge(top[r], acc);
+      for (int m = 16; m > 0; m >>= 1) acc = top4_merge(acc, top4_shfl_xor(acc, m));
+      if (lane == 0) top[r] = top4_merge(top[r], acc);
     };
 
     __syncthreads();  // profile and ring ready
@@ -380,8 +380,10 @@ __global__ void __launch_bounds__(NT, MINB) k_scan(ScanArgs a) {
     __syncthreads();
     if (tid < RG) {
       const int p = g * RG + tid;
-      const Top2 v = top[tid];
-      a.partial[(size_t)p * a.n_chunks + c] = make_int4(v.s1, v.f1, v.s2, v.f2);
+      const Top4 v = top[tid];
+      int4* dst = a.partial + ((size_t)p * a.n_chunks + c) * 2;   // top-4 of this chunk
+      dst[0] = make_int4(v.s[0], v.f[0], v.s[1], v.f[1]);
+      dst[1] = make_int4(v.s[2], v.f[2], v.s[3], v.f[3]);
     }
     // the next item rewrites the profile, ring and summaries only after the barrier at its top
   }
@@ -497,13 +499,25 @@ __global__ void __launch_bounds__(kFinWarps * 32) k_finalize(FinalArgs a) {
   int64_t l = a.offsets[ridx + 1] - off;
   const int32_t m = l < 0 ? 0 : (l > MSS_MAX_READ_LEN ? MSS_MAX_READ_LEN : (int32_t)l);
 
-  Top2 acc = top2_empty();
+  Top4 t4 = top4_empty();
   for (int c = lane; c < a.n_chunks; c += 32) {
-    const int4 v = a.partial[(size_t)p * a.n_chunks + c];
-    acc = top2_merge(acc, Top2{v.x, v.y, v.z, v.w});
+    const int4 v0 = a.partial[((size_t)p * a.n_chunks + c) * 2];
+    const int4 v1 = a.partial[((size_t)p * a.n_chunks + c) * 2 + 1];
+    Top4 v;
+    v.s[0] = v0.x, v.f[0] = v0.y, v.s[1] = v0.z, v.f[1] = v0.w;
+    v.s[2] = v1.x, v.f[2] = v1.y, v.s[3] = v1.z, v.f[3] = v1.w;
+    t4 = top4_merge(t4, v);
   }
 #pragma unroll
-  for (int s = 16; s > 0; s >>= 1) acc = top2_merge(acc, top2_shfl_xor(acc, s));
+  for (int s = 16; s > 0; s >>= 1) t4 = top4_merge(t4, top4_shfl_xor(t4, s));
+  // the best fragment and the second: the next entry, or with the neighbour rule the first
+  // entry not adjacent to the best (at most two entries are adjacent, so the top-4 holds it)
+  Top2 acc{t4.s[0], t4.f[0], -1, 0x7fffffff};
+#pragma unroll
+  for (int i = 3; i >= 1; --i) {
+    const bool adjacent = t4.f[i] == t4.f[0] - 1 || t4.f[i] == t4.f[0] + 1;
+    if (t4.s[i] >= 0 && !(a.exclude_neighbors && adjacent)) acc.s2 = t4.s[i], acc.f2 = t4.f[i];
+  }
 
   for (int k = lane; k < m; k += 32) {
     uint32_t cf = ascii_code((uint8_t)a.reads[off + k]);

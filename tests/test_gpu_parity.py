@@ -363,3 +363,27 @@ def test_pssm_constant_quality_equals_plain_scores_and_errors(mss):
     with pytest.raises(mss.MssError):
         mss.mss_map_reads_quals_device(g, d_seq, d_q, d_off, R, 150, 5, -4, 40, d_hits)   # scale above 32
     g.close()
+
+
+# ---------------------------------------------------------------- second fragment not adjacent to the best
+@pytest.mark.parametrize("F", [1000, 333])
+def test_second_rule_excluding_neighbours(mss, F):
+    """With the neighbour rule the second is the best fragment not adjacent to the best, bit for
+    bit against the oracle; reads straddling fragment borders make the plain second a
+    neighbour often.  Switching back gives the plain result."""
+    wl = gen.workloads()["tiny-50k"]
+    genome, reads = gen.materialize(wl)
+    g_ascii = bytes(genome)
+    strs = [bytes(reads.read(i)) for i in range(reads.count)]
+    strs += [g_ascii[b - 40:b + 60] for b in range(F, 20 * F, 2 * F)]   # junction reads
+    seq, off = concat_reads(strs)
+    g = mss.mss_load_genome(genome, frag_len=F, max_read_len=100)
+    mss.mss_set_second_rule(g, True)
+    got = mss.mss_map_reads(g, seq, off, wl.match, wl.mismatch)
+    want, _, _ = oracle.map_batch(genome, F, seq, off, wl.match, wl.mismatch, exclude_neighbors=True)
+    assert_hits_equal(got, want, f"neighbour rule F={F}")
+    plain, _, _ = oracle_map(genome, F, seq, off, wl.match, wl.mismatch, procs=cpu_count())
+    assert np.any(plain["second_frag"] != want["second_frag"])   # the rule changed something
+    mss.mss_set_second_rule(g, False)
+    assert_hits_equal(mss.mss_map_reads(g, seq, off, wl.match, wl.mismatch), plain, "plain rule again")
+    g.close()

@@ -160,6 +160,13 @@ def test_proposed_with_all_fragments_equals_exhaustive(mss):
     got = mss.hits_from_bytes(d_out.cpu())
     want = mss.mss_map_reads(g, reads.seq, reads.offsets, 5, -4)
     assert_hits_equal(got, want, "K = NF")
+    # the neighbour rule of the context applies to the rescored candidates as well
+    mss.mss_set_second_rule(g, True)
+    d_out.zero_()
+    prop.map_reads(g, dev(reads.seq), dev(reads.offsets), R, 150, 5, -4, NF, -1e30, d_out)
+    assert_hits_equal(mss.hits_from_bytes(d_out.cpu()), mss.mss_map_reads(g, reads.seq, reads.offsets, 5, -4),
+                      "K = NF, neighbour rule")
+    mss.mss_set_second_rule(g, False)
     # everything falls back: the exhaustive path
     d_out.zero_()
     nfb = prop.map_reads(g, dev(reads.seq), dev(reads.offsets), R, 150, 5, -4, 4, 1e30, d_out)
