@@ -75,6 +75,13 @@ def workload(args, rank: int):
     return wl, genome, seq, off
 
 
+# DRAM bytes (read + write) of one k_scan launch of the default workload (bact-4.6M, all
+# 400,000 reads, F = 2048, read step 1), from one ncu capture of that launch with
+# dram__bytes_read.sum and dram__bytes_write.sum (one pass); the capture and its command are in
+# profiles/launches_bact-4.6M_400k-reads.md.  Other workloads report no traffic.
+SCAN_DRAM_BYTES_DEFAULT = 59.66e6
+
+
 def cells_of(lengths: np.ndarray, G: int, F: int, step: int = 1) -> int:
     """Scan cells: read positions taking part (every base, or every other one with read step 2)
     x padded diagonals x 2 strands."""
@@ -348,6 +355,9 @@ def main():
         # the integer/DPX pipe alone, measured by the library's pipe probe: warp-instructions per
         # SM clock x 32 threads x 2 lanes / 2 ops per cell, at the same clock
         dpx_only = probe[0] * 32 * sms * 2070.0e6 / 1e12 if probe else None
+        default_run = (wl.name == gen.workloads()[args.workload].name and args.workload == "bact-4.6M"
+                       and args.read_step == 1 and not args.autotune and info["frag_len"] == 2048)
+        traffic = SCAN_DRAM_BYTES_DEFAULT if default_run else None
         scan_mean_ms = statistics.mean(scan_ms)
         achieved = cells_step / (scan_mean_ms * 1e-3) / 1e12
         tune = mss.mss_get_tune(g)
@@ -366,7 +376,7 @@ def main():
             "gpu_launches": int(launches),
             "roofline": {"bound": "alu", "kernel": "k_scan (phase-one scan + fragment top-2)",
                          "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "Tcell/s",
-                         "frac": round(achieved / peak, 4), "traffic": None,
+                         "frac": round(achieved / peak, 4), "traffic": traffic,
                          "peak_source": f"derived: {sms} SMs x 4 sub-partitions x 32 cells/clk (16-lane integer/DPX "
                                         "pipe + 16-lane FMA pipe, packed 16-bit x2, 2 ops per cell) x 2070 MHz",
                          "scan_ms_per_step": round(scan_mean_ms, 3),

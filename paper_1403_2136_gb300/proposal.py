@@ -17,6 +17,7 @@ Every compute step runs in libmaxss kernels; this module draws batches and keeps
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import sys
@@ -103,7 +104,9 @@ def main(argv=None):
     import gen
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("--genome-len", type=int, default=23_000_000, help="chromosome-shaped genome length")
+    ap.add_argument("--workload", default="chrom-230M", choices=["chrom-230M", "ancient-2.4G"],
+                    help="genome and read shape (the genome is scaled to --genome-len)")
+    ap.add_argument("--genome-len", type=int, default=23_000_000, help="genome length (0: the workload's own)")
     ap.add_argument("--train-reads", type=int, default=60_000)
     ap.add_argument("--eval-reads", type=int, default=20_000)
     ap.add_argument("--steps", type=int, default=800)
@@ -116,15 +119,17 @@ def main(argv=None):
     args = ap.parse_args(argv)
     log = lambda m: print(m, file=sys.stderr, flush=True)  # noqa: E731
 
-    wl = gen.workloads()["chrom-230M"]
-    wl = gen.scaled(wl, genome_len=args.genome_len)
+    wl = gen.workloads()[args.workload]
+    if args.genome_len:
+        wl = gen.scaled(wl, genome_len=args.genome_len)
+    t0 = time.perf_counter()
     genome = gen.make_genome(wl.genome, wl.seed)
-    F, max_len = 2048, 250
+    log(f"genome of {genome.shape[0]} bases in {time.perf_counter() - t0:.1f} s")
+    F = 2048
     spec = wl.reads[0]
-    tr = gen.make_reads(genome, gen.ReadSpec(args.train_reads, lengths=spec.lengths, sub_levels=spec.sub_levels),
-                        wl.seed * 7 + 1)
-    ev = gen.make_reads(genome, gen.ReadSpec(args.eval_reads, lengths=spec.lengths, sub_levels=spec.sub_levels),
-                        wl.seed * 7 + 2)
+    max_len = 250 if spec.lognormal is None else int(spec.lognormal[3])
+    tr = gen.make_reads(genome, dataclasses.replace(spec, count=max(args.train_reads, 1)), wl.seed * 7 + 1)
+    ev = gen.make_reads(genome, dataclasses.replace(spec, count=args.eval_reads), wl.seed * 7 + 2)
     g = mss_load_genome(genome, frag_len=F, max_read_len=max_len)
     NF = g.info()["num_frags"]
     d_tseq, d_toff = _dev(torch, tr.seq), _dev(torch, tr.offsets)
@@ -135,7 +140,7 @@ def main(argv=None):
     prop = Proposal(seed=1)
     t0 = time.perf_counter()
     losses = train(torch, prop, g, d_tseq, d_toff, tr.lengths, labels, F, max_len, args.steps, args.batch, args.lr,
-                   args.temperature, log=log)
+                   args.temperature, log=log) if args.steps > 0 else []
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     if args.checkpoint:
@@ -155,8 +160,10 @@ def main(argv=None):
     line = {"metric": "learned proposal + exact rescoring vs exhaustive scan (top-1 agreement, recall, speedup)",
             "workload": wl.name, "genome_bp": int(genome.shape[0]), "frag_len": F, "num_frags": int(NF),
             "train_reads": tr.count, "train_steps": args.steps, "batch": args.batch,
-            "loss_first": round(losses[0], 4), "loss_last": round(float(np.mean(losses[-20:])), 4),
-            "loss_curve": [round(float(np.mean(c)), 4) for c in np.array_split(np.asarray(losses), min(10, len(losses)))],
+            "loss_first": round(losses[0], 4) if losses else None,
+            "loss_last": round(float(np.mean(losses[-20:])), 4) if losses else None,
+            "loss_curve": [round(float(np.mean(c)), 4) for c in np.array_split(np.asarray(losses), min(10, len(losses)))]
+            if losses else [],
             "label_s": round(label_s, 2), "train_s": round(train_s, 2), "index_s": round(index_s, 2),
             "eval_reads": ev.count, "exhaustive_ms": round(ex_ms, 1),
             "exhaustive_reads_per_s": round(ev.count / (ex_ms / 1e3), 1), "K": args.K, "results": res}
