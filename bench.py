@@ -27,6 +27,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 from concurrent.futures import ProcessPoolExecutor
 
@@ -173,9 +174,11 @@ class ClockSampler:
 
     def __init__(self, gpu_index: int):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        # samples go to a file given by MSS_CLOCK_LOG, else to a temporary file removed after reading
+        self.keep = "MSS_CLOCK_LOG" in os.environ
+        self.path = os.environ.get("MSS_CLOCK_LOG") or os.path.join(tempfile.gettempdir(),
+                                                                      f"mss_clocks_{os.getpid()}.csv")
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={','.join(self.FIELDS)}",
                                           "--format=csv,noheader,nounits", "-lms", "200", "-i", str(gpu_index)],
@@ -194,7 +197,11 @@ class ClockSampler:
         self.fh.close()
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        with open(self.path) as fh:
+            lines = fh.readlines()
+        if not self.keep:
+            os.remove(self.path)
+        for line in lines:
             p = [x.strip() for x in line.split(",")]
             if len(p) < 8:
                 continue

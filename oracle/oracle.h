@@ -18,7 +18,7 @@
  *   - "Second phase of MaxSSmap": Needleman-Wunsch of the read against the region found in
  *     phase one, match 5, mismatch -4, gap -26 by default.
  *
- * Readings where the paper is silent (each restated in the design doc):
+ * Readings where the paper is silent:
  *   - both strands are scanned; the reverse strand is the reverse complement of the read;
  *   - only diagonals d in [0, Gp) exist (no left overhang);
  *   - per-fragment argmax tie: strand + before -, then smallest d;

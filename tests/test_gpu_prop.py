@@ -372,7 +372,7 @@ def test_trainer_end_to_end_small(mss, capsys):
                    "--batch", "64", "--taus=-1e30,1e30"])
     out = capsys.readouterr().out.strip().splitlines()[-1]
     line = json.loads(out)
-    # learning itself is pinned by the fixed-batch step test; here the driver's plumbing
+    # learning itself is pinned by the fixed-batch step test; here the trainer's end-to-end plumbing
     assert np.isfinite(line["loss_first"]) and np.isfinite(line["loss_last"])
     r_all, r_fallback = line["results"]
     assert r_fallback["fallback_reads"] == line["eval_reads"]
