@@ -83,6 +83,15 @@ def workload(args, rank: int):
 SCAN_DRAM_BYTES_DEFAULT = 59.66e6
 
 
+def workload_config(wl, genome, lengths, F: int, args, world: int = 1) -> dict:
+    """The `config` object both arms report for the same workload."""
+    Gp = -(-int(genome.shape[0]) // F) * F
+    return {"workload": wl.name, "genome_bp": int(genome.shape[0]), "frag_len": F, "padded_bp": Gp,
+            "reads": int(lengths.shape[0]), "read_lengths": sorted(set(np.asarray(lengths).tolist())),
+            "scores": [wl.match, wl.mismatch], "nw": list(wl.nw),
+            "parallelism": f"replicas x{world} (read batches per GPU)", "read_step": args.read_step}
+
+
 def cells_of(lengths: np.ndarray, G: int, F: int, step: int = 1) -> int:
     """Scan cells: read positions taking part (every base, or every other one with read step 2)
     x padded diagonals x 2 strands."""
@@ -155,8 +164,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": round(gcups, 4), "unit": "GCUPS", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(tot_t / args.steps * 1e3, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": wl.name, "genome_bp": int(genome.shape[0]), "frag_len": wl.frag_len,
-                   "read_step": args.read_step},
+        "config": workload_config(wl, genome, np.diff(off), wl.frag_len, args, args.gpus),
         "reads_per_s": round(tot_reads / tot_t, 3),
         "cpu_baseline": {"value": round(gcups, 4), "unit": "GCUPS", "cores": cores, "kind": "oracle",
                          "sample": sample},
@@ -372,12 +380,9 @@ def main():
             "metric": METRIC, "value": round(gcups, 3), "unit": "GCUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(t * 1e3 / args.steps, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int16", "data": "synthetic",
-            "config": {"workload": wl.name, "genome_bp": int(genome.shape[0]), "frag_len": info["frag_len"],
-                       "padded_bp": info["padded_len"], "reads": R, "read_lengths": sorted(set(lengths.tolist())),
-                       "scores": [wl.match, wl.mismatch], "nw": list(wl.nw),
+            "config": {**workload_config(wl, genome, lengths, info["frag_len"], args, world),
                        "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
-                       "parallelism": f"replicas x{world} (read batches per GPU)", "scan_tune": tune,
-                       "read_step": args.read_step, "autotune": tuned},
+                       "scan_tune": tune, "autotune": tuned},
             "reads_per_s": round(reads_s, 1),
             "e2e": e2e,
             "gpu_launches": int(launches),
