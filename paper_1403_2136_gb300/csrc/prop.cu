@@ -616,6 +616,23 @@ __global__ void k_window_codes(const uint32_t* __restrict__ g2, const uint32_t* 
   if (threadIdx.x == 0) lens[i] = len;
 }
 
+// fallback reads: gather the selected reads into a compact batch (one warp per read) and
+// scatter their hits back to the reads' places
+__global__ void k_gather_reads(const char* __restrict__ reads, const int64_t* __restrict__ offsets,
+                               const int32_t* __restrict__ sel, int32_t n, const int64_t* __restrict__ new_off,
+                               char* __restrict__ out) {
+  const int w = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (w >= n) return;
+  const int64_t src = offsets[sel[w]], len = new_off[w + 1] - new_off[w];
+  for (int64_t k = lane; k < len; k += 32) out[new_off[w] + k] = reads[src + k];
+}
+
+__global__ void k_scatter_hits(const mss_hit* __restrict__ sub, const int32_t* __restrict__ sel, int32_t n,
+                               mss_hit* __restrict__ out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) out[sel[j]] = sub[j];
+}
+
 // deterministic initialisation: uniform(-a, a) with a = sqrt(6 / fan_in), biases 0.01; the
 // uniform draw is a SplitMix64-style hash of (seed, index)
 __device__ __forceinline__ float hash_uniform(uint64_t seed, uint64_t i) {
@@ -657,6 +674,20 @@ cudaError_t prop_window_codes(const uint32_t* g2, const uint32_t* gm, const int6
                               int32_t ld, uint8_t* codes, int32_t* lens, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   k_window_codes<<<n, 256, 0, s>>>(g2, gm, starts, n, len, ld, codes, lens);
+  return cudaGetLastError();
+}
+
+cudaError_t prop_gather_reads(const char* reads, const int64_t* offsets, const int32_t* sel, int32_t n,
+                              const int64_t* new_off, char* out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_gather_reads<<<(unsigned)((n + 7) / 8), 256, 0, s>>>(reads, offsets, sel, n, new_off, out);
+  return cudaGetLastError();
+}
+
+cudaError_t prop_scatter_hits(const void* sub, const int32_t* sel, int32_t n, void* out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_scatter_hits<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(static_cast<const mss_hit*>(sub), sel, n,
+                                                             static_cast<mss_hit*>(out));
   return cudaGetLastError();
 }
 

@@ -79,6 +79,11 @@ cudaError_t prop_read_codes(const char* reads, const int64_t* offsets, const int
 cudaError_t prop_window_codes(const uint32_t* g2, const uint32_t* gm, const int64_t* starts, int32_t n, int32_t len,
                               int32_t ld, uint8_t* codes, int32_t* lens, cudaStream_t s);
 cudaError_t prop_init_params(float* w, uint64_t seed, cudaStream_t s);
+// fallback batch: reads sel[0..n) copied to out at new_off (n + 1 prefix offsets), and the
+// batch's hits (mss_hit) written back to out[sel[j]]
+cudaError_t prop_gather_reads(const char* reads, const int64_t* offsets, const int32_t* sel, int32_t n,
+                              const int64_t* new_off, char* out, cudaStream_t s);
+cudaError_t prop_scatter_hits(const void* sub, const int32_t* sel, int32_t n, void* out, cudaStream_t s);
 cudaError_t prop_to_bf16(const float* w, __nv_bfloat16* wb, int64_t n, cudaStream_t s);
 
 }  // namespace mss

@@ -484,29 +484,25 @@ mss_status mss_map_reads_proposed(mss_ctx* ctx, mss_prop* p, const char* d_reads
   PCK(cudaMemcpy(hoff.data(), d_offsets, (size_t)(R + 1) * 8, cudaMemcpyDeviceToHost), "offsets read");
   std::vector<int64_t> noff(fb.size() + 1, 0);
   for (size_t j = 0; j < fb.size(); ++j) noff[j + 1] = noff[j] + (hoff[fb[j] + 1] - hoff[fb[j]]);
-  Buf sub_reads, sub_off, sub_hits;
+  const int32_t nfb = (int32_t)fb.size();
+  Buf sub_reads, sub_off, sub_hits, sel;
   PCK(sub_reads.ensure((size_t)noff.back() + 16), "fallback reads");
   PCK(sub_off.ensure(noff.size() * 8), "fallback offsets");
   PCK(sub_hits.ensure(fb.size() * sizeof(mss_hit)), "fallback hits");
-  for (size_t j = 0; j < fb.size(); ++j)
-    PCK(cudaMemcpyAsync(sub_reads.as<char>() + noff[j], d_reads + hoff[fb[j]], (size_t)(noff[j + 1] - noff[j]),
-                        cudaMemcpyDeviceToDevice, s),
-        "gather");
+  PCK(sel.ensure(fb.size() * 4), "fallback reads");
   PCK(cudaMemcpyAsync(sub_off.p, noff.data(), noff.size() * 8, cudaMemcpyHostToDevice, s), "fallback offsets");
-  mss_status st = mss_map_reads_device(ctx, sub_reads.as<char>(), sub_off.as<int64_t>(), (int32_t)fb.size(), max_len, sp,
-                                       sub_hits.as<mss_hit>(), nullptr);
-  if (!st) st = mss_sync(ctx, nullptr);
-  if (!st) {
-    for (size_t j = 0; j < fb.size(); ++j) {
-      cudaError_t e = cudaMemcpyAsync(d_out + fb[j], sub_hits.as<mss_hit>() + j, sizeof(mss_hit),
-                                      cudaMemcpyDeviceToDevice, s);
-      if (e != cudaSuccess) {
-        st = set_error(MSS_ECUDA, "scatter");
-        break;
-      }
-    }
-    if (!st && cudaStreamSynchronize(s) != cudaSuccess) st = set_error(MSS_ECUDA, "sync");
-  }
+  PCK(cudaMemcpyAsync(sel.p, fb.data(), fb.size() * 4, cudaMemcpyHostToDevice, s), "fallback reads");
+  PCK(prop_gather_reads(d_reads, d_offsets, sel.as<int32_t>(), nfb, sub_off.as<int64_t>(), sub_reads.as<char>(), s),
+      "gather");
+  p->launches += 1;
+  mss_status st = mss_map_reads_device(ctx, sub_reads.as<char>(), sub_off.as<int64_t>(), nfb, max_len, sp,
+                                       sub_hits.as<mss_hit>(), stream);
+  if (!st) st = mss_sync(ctx, stream);
+  if (!st && prop_scatter_hits(sub_hits.p, sel.as<int32_t>(), nfb, d_out, s) != cudaSuccess)
+    st = set_error(MSS_ECUDA, "scatter");
+  if (!st && cudaStreamSynchronize(s) != cudaSuccess) st = set_error(MSS_ECUDA, "sync");
+  if (!st) p->launches += 1;
+  sel.release();
   sub_reads.release();
   sub_off.release();
   sub_hits.release();
