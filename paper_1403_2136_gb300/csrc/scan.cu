@@ -203,6 +203,19 @@ __global__ void __launch_bounds__(NT, MINB) k_scan(ScanArgs a) {
                   &mbar[buf]);
     };
     auto fold = [&](int r, int32_t lo, int32_t hi) {  // fragments [lo, hi) of read r, one warp
+      if (hi - lo <= 8) {  // the usual case (F >= a tile / 8): one lane inserts them in order
+        if (lane == 0) {
+          Top4 t = top[r];
+          for (int32_t f = lo; f < hi; ++f) {
+            const int slot = r * S + (int)(f % S);
+            t = top4_insert(t, ring[slot], f);
+            ring[slot] = 0;
+          }
+          top[r] = t;
+        }
+        __syncwarp();
+        return;
+      }
       Top4 acc = top4_empty();
       for (int32_t base = lo; base < hi; base += 32) {
         const int32_t f = base + lane;
