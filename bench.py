@@ -370,6 +370,12 @@ def main():
         # the integer/DPX pipe alone, measured by the library's pipe probe: warp-instructions per
         # SM clock x 32 threads x 2 lanes / 2 ops per cell, at the same clock
         dpx_only = probe[0] * 32 * sms * 2070.0e6 / 1e12 if probe else None
+        # the 16-bit lanes the scan ran on: f16 x2 (integers up to 2048, exact) when every partial
+        # sum fits and both scores have an f16 form with a zero low byte, else int16 x2
+        f16_ok = (max_len * wl.match <= 2048 and all(float(np.float16(v)) == v and
+                  (int(np.array(v, np.float16).view(np.uint16)) & 0xFF) == 0 for v in (wl.match, wl.mismatch)))
+        variant = tune["variant"] if tune["variant"] >= 0 else (1 if f16_ok else 0)
+        lanes = "f16x2, exact integers <= 2048" if variant == 1 else "int16x2"
         default_run = (wl.name == gen.workloads()[args.workload].name and args.workload == "bact-4.6M"
                        and args.read_step == 1 and not args.autotune and info["frag_len"] == 2048)
         traffic = SCAN_DRAM_BYTES_DEFAULT if default_run else None
@@ -382,7 +388,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "int16", "data": "synthetic",
             "config": {**workload_config(wl, genome, lengths, info["frag_len"], args, world),
                        "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
-                       "scan_tune": tune, "autotune": tuned},
+                       "scan_tune": tune, "autotune": tuned, "scan_lanes": lanes},
             "reads_per_s": round(reads_s, 1),
             "e2e": e2e,
             "gpu_launches": int(launches),
