@@ -80,7 +80,7 @@ def workload(args, rank: int):
 # 400,000 reads, F = 2048, read step 1), from one ncu capture of that launch with
 # dram__bytes_read.sum and dram__bytes_write.sum (one pass); the capture and its command are in
 # profiles/launches_bact-4.6M_400k-reads.md.  Other workloads report no traffic.
-SCAN_DRAM_BYTES_DEFAULT = 59.66e6
+SCAN_DRAM_BYTES_DEFAULT = 60.29e6
 
 
 def workload_config(wl, genome, lengths, F: int, args, world: int = 1) -> dict:
@@ -392,7 +392,7 @@ def main():
             "reads_per_s": round(reads_s, 1),
             "e2e": e2e,
             "gpu_launches": int(launches),
-            "roofline": {"bound": "alu", "kernel": "k_scan (phase-one scan + fragment top-2)",
+            "roofline": {"bound": "alu", "kernel": "k_scan (phase-one scan + per-read fragment top-4)",
                          "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "Tcell/s",
                          "frac": round(achieved / peak, 4), "traffic": traffic,
                          "peak_source": f"derived: {sms} SMs x 4 sub-partitions x 32 cells/clk (16-lane integer/DPX "
