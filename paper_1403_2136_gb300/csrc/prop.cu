@@ -59,28 +59,66 @@ __device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, uint32_t b
 
 // ------------------------------------------------------------------------------------------
 // layer 1: out[n][p][co] = relu(b[co] + sum_t w1[t][x[p+t-3]][co]) for p < len, else 0
-__global__ void k_embed_l1(const uint8_t* __restrict__ codes, const int32_t* __restrict__ lens, int32_t ld_codes,
-                           const float* __restrict__ w1, const float* __restrict__ b1, __nv_bfloat16* __restrict__ out,
-                           int32_t rows) {
+// thread = (position, group of 8 channels); a CTA covers 64 positions of one sequence, 16 at a
+// time; the per-channel sums run in the same order as the definition (bias, then taps 0 .. 6)
+constexpr int kL1Pos = 64;
+__global__ void __launch_bounds__(256) k_embed_l1(const uint8_t* __restrict__ codes, const int32_t* __restrict__ lens,
+                                                  int32_t ld_codes, const float* __restrict__ w1,
+                                                  const float* __restrict__ b1, __nv_bfloat16* __restrict__ out,
+                                                  int32_t rows) {
   const int n = blockIdx.y;
-  const int p = blockIdx.x * 2 + (threadIdx.x >> 7);
-  const int co = threadIdx.x & 127;
+  const int g = threadIdx.x & 15;
   const int len = lens[n];
-  if (p >= rows - 6) return;
-  float v = 0.f;
-  if (p < len) {
-    v = b1[co];
+  const int p_end = min(rows - 6, (int)(blockIdx.x + 1) * kL1Pos);
+  const uint8_t* cn = codes + (int64_t)n * ld_codes;
+  for (int p = blockIdx.x * kL1Pos + (threadIdx.x >> 4); p < p_end; p += 16) {
+    float v[8];
 #pragma unroll
-    for (int t = 0; t < kPropTaps; ++t) {
-      const int q = p + t - 3;
-      if (q >= 0 && q < len) {
-        const uint32_t c = codes[(int64_t)n * ld_codes + q];
-        if (c < 4) v += w1[(t * 4 + c) * kPropC + co];
+    for (int j = 0; j < 8; ++j) v[j] = 0.f;
+    if (p < len) {
+      const float4 bA = *reinterpret_cast<const float4*>(b1 + 8 * g);
+      const float4 bB = *reinterpret_cast<const float4*>(b1 + 8 * g + 4);
+      v[0] = bA.x, v[1] = bA.y, v[2] = bA.z, v[3] = bA.w, v[4] = bB.x, v[5] = bB.y, v[6] = bB.z, v[7] = bB.w;
+#pragma unroll
+      for (int t = 0; t < kPropTaps; ++t) {
+        const int q = p + t - 3;
+        if (q >= 0 && q < len) {
+          const uint32_t c = cn[q];
+          if (c < 4) {
+            const float4* wr = reinterpret_cast<const float4*>(w1 + (t * 4 + c) * kPropC + 8 * g);
+            const float4 wA = wr[0], wB = wr[1];
+            v[0] += wA.x, v[1] += wA.y, v[2] += wA.z, v[3] += wA.w;
+            v[4] += wB.x, v[5] += wB.y, v[6] += wB.z, v[7] += wB.w;
+          }
+        }
       }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = fmaxf(v[j], 0.f);
     }
-    v = fmaxf(v, 0.f);
+    uint32_t w[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+      w[j] = *reinterpret_cast<uint32_t*>(&h);
+    }
+    *reinterpret_cast<uint4*>(out + ((int64_t)n * rows + p + 3) * kPropC + 8 * g) = make_uint4(w[0], w[1], w[2], w[3]);
   }
-  out[((int64_t)n * rows + p + 3) * kPropC + co] = __float2bfloat16(v);
+}
+
+// zero the three halo rows on each side of every sequence of up to four activation buffers
+// (the layers write every other row)
+__global__ void k_zero_halo(__nv_bfloat16* b0, __nv_bfloat16* b1, __nv_bfloat16* b2, __nv_bfloat16* b3, int32_t n,
+                            int32_t rows) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // (sequence, halo row, 16-byte chunk)
+  if (e >= (int64_t)n * 6 * 16) return;
+  const int64_t seq = e / 96;
+  const int r = (int)(e % 96) >> 4, c = (int)(e & 15);
+  const int row = r < 3 ? r : rows - 6 + r;
+  const int64_t off = (seq * rows + row) * kPropC + 8 * c;
+  __nv_bfloat16* bs[4] = {b0, b1, b2, b3};
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    if (bs[i]) *reinterpret_cast<uint4*>(bs[i] + off) = make_uint4(0, 0, 0, 0);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -220,29 +258,57 @@ __global__ void k_l1_wgrad(const uint8_t* __restrict__ codes, const int32_t* __r
 
 // ------------------------------------------------------------------------------------------
 // max over positions p < len (first maximum), L2 norm.  One CTA (128 threads) per sequence.
-__global__ void k_pool_norm(const __nv_bfloat16* __restrict__ act, const int32_t* __restrict__ lens, int32_t rows,
-                            float* __restrict__ emb, float* __restrict__ norms, int32_t* __restrict__ argmax) {
-  const int n = blockIdx.x, co = threadIdx.x;
+// max over the positions of each channel (first argmax kept), then the L2 norm.  CTA = one
+// sequence, 256 threads = 16 position lanes x 16 groups of 8 channels; the lanes' maxima
+// merge with ties going to the lower position, so the result is the first maximum.
+__global__ void __launch_bounds__(256) k_pool_norm(const __nv_bfloat16* __restrict__ act,
+                                                   const int32_t* __restrict__ lens, int32_t rows,
+                                                   float* __restrict__ emb, float* __restrict__ norms,
+                                                   int32_t* __restrict__ argmax) {
+  const int n = blockIdx.x, tid = threadIdx.x;
+  const int g = tid & 15, pl = tid >> 4;
   const int len = lens[n];
-  float best = -1.f;
-  int bi = 0;
-  for (int p = 0; p < len; ++p) {
-    const float v = __bfloat162float(act[((int64_t)n * rows + p + 3) * kPropC + co]);
-    if (v > best) {
-      best = v;
-      bi = p;
+  float best[8];
+  int bi[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) best[j] = -1.f, bi[j] = 0;
+  const __nv_bfloat16* an = act + ((int64_t)n * rows + 3) * kPropC + 8 * g;
+#pragma unroll 4
+  for (int p = pl; p < len; p += 16) {
+    const uint4 u = *reinterpret_cast<const uint4*>(an + (int64_t)p * kPropC);
+    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162*>(&w[j]);
+      const float v0 = __bfloat162float(h.x), v1 = __bfloat162float(h.y);
+      if (v0 > best[2 * j]) best[2 * j] = v0, bi[2 * j] = p;
+      if (v1 > best[2 * j + 1]) best[2 * j + 1] = v1, bi[2 * j + 1] = p;
     }
   }
-  if (len <= 0) best = 0.f;
+  __shared__ float s_best[16][kPropC];
+  __shared__ int s_bi[16][kPropC];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) s_best[pl][8 * g + j] = best[j], s_bi[pl][8 * g + j] = bi[j];
+  __syncthreads();
+  if (tid >= kPropC) return;
+  const int co = tid;
+  float b = -1.f;
+  int bp = 0;
+  for (int l = 0; l < 16; ++l) {
+    const float v = s_best[l][co];
+    const int q = s_bi[l][co];
+    if (v > b || (v == b && v >= 0.f && q < bp)) b = v, bp = q;
+  }
+  if (len <= 0) b = 0.f, bp = 0;
   __shared__ float red[4];
-  float sq = best * best;
+  float sq = b * b;
 #pragma unroll
   for (int s = 16; s > 0; s >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, s);
   if ((co & 31) == 0) red[co >> 5] = sq;
-  __syncthreads();
+  asm volatile("bar.sync 1, 128;" ::: "memory");
   const float nrm = sqrtf(red[0] + red[1] + red[2] + red[3]) + 1e-6f;
-  emb[n * kPropC + co] = best / nrm;
-  if (argmax) argmax[n * kPropC + co] = bi;
+  emb[n * kPropC + co] = b / nrm;
+  if (argmax) argmax[n * kPropC + co] = bp;
   if (norms && co == 0) norms[n] = nrm;
 }
 
@@ -494,8 +560,16 @@ __global__ void k_topk(const float* __restrict__ scores, int64_t NF, int32_t K, 
 // host launchers
 cudaError_t prop_embed_l1(const uint8_t* codes, const int32_t* lens, int32_t ld, int32_t n, const float* w1,
                           const float* b1, __nv_bfloat16* out, int32_t rows, cudaStream_t s) {
-  dim3 grid((unsigned)((rows - 6 + 1) / 2), (unsigned)n);
+  dim3 grid((unsigned)((rows - 6 + kL1Pos - 1) / kL1Pos), (unsigned)n);
   k_embed_l1<<<grid, 256, 0, s>>>(codes, lens, ld, w1, b1, out, rows);
+  return cudaGetLastError();
+}
+
+cudaError_t prop_zero_halo(__nv_bfloat16* b0, __nv_bfloat16* b1, __nv_bfloat16* b2, __nv_bfloat16* b3, int32_t n,
+                           int32_t rows, cudaStream_t s) {
+  const int64_t work = (int64_t)n * 96;
+  if (work <= 0) return cudaSuccess;
+  k_zero_halo<<<(unsigned)((work + 255) / 256), 256, 0, s>>>(b0, b1, b2, b3, n, rows);
   return cudaGetLastError();
 }
 
@@ -532,7 +606,7 @@ cudaError_t prop_l1_wgrad(const uint8_t* codes, const int32_t* lens, int32_t ld,
 
 cudaError_t prop_pool_norm(const __nv_bfloat16* act, const int32_t* lens, int32_t n, int32_t rows, float* emb,
                            float* norms, int32_t* argmax, cudaStream_t s) {
-  k_pool_norm<<<n, kPropC, 0, s>>>(act, lens, rows, emb, norms, argmax);
+  k_pool_norm<<<n, 256, 0, s>>>(act, lens, rows, emb, norms, argmax);
   return cudaGetLastError();
 }
 

@@ -21,6 +21,9 @@ inline int64_t prop_off_b(int layer) { return prop_off_w(layer) + kPropWl; }
 // rows of an activation buffer for sequences of at most maxlen positions
 inline int32_t prop_rows(int32_t maxlen) { return ((maxlen + 127) / 128) * 128 + 6; }
 
+// zero the 3 halo rows on each side of every sequence of up to four activation buffers (null = skip)
+cudaError_t prop_zero_halo(__nv_bfloat16* b0, __nv_bfloat16* b1, __nv_bfloat16* b2, __nv_bfloat16* b3, int32_t n,
+                           int32_t rows, cudaStream_t s);
 cudaError_t prop_embed_l1(const uint8_t* codes, const int32_t* lens, int32_t ld, int32_t n, const float* w1,
                           const float* b1, __nv_bfloat16* out, int32_t rows, cudaStream_t s);
 // 128 -> 128 conv on the tensor cores (conv_tc.cu).  wcanon: the layer's weights w[t][in][out]

@@ -103,8 +103,10 @@ mss_status forward(mss_prop* p, const uint8_t* codes, const int32_t* lens, int32
                    Acts& a, cudaStream_t s) {
   const int32_t rows = prop_rows(maxlen);
   PCK(a.ensure(n, rows), "activation buffers");
-  const size_t abytes = (size_t)n * rows * kPropC * sizeof(__nv_bfloat16);
-  for (auto& b : a.act) PCK(cudaMemsetAsync(b.p, 0, abytes, s), "activation clear");
+  // every row but the halo is written by the layers below
+  PCK(prop_zero_halo(a.act[0].as<__nv_bfloat16>(), a.act[1].as<__nv_bfloat16>(), a.act[2].as<__nv_bfloat16>(),
+                     a.act[3].as<__nv_bfloat16>(), n, rows, s),
+      "activation halo");
   const float* w = p->w32.as<float>();
   PCK(prop_embed_l1(codes, lens, ld, n, w, w + prop_off_b1(), a.act[0].as<__nv_bfloat16>(), rows, s), "layer 1");
   for (int l = 2; l <= 4; ++l)
@@ -114,7 +116,7 @@ mss_status forward(mss_prop* p, const uint8_t* codes, const int32_t* lens, int32
   PCK(prop_pool_norm(a.act[3].as<__nv_bfloat16>(), lens, n, rows, a.emb.as<float>(), a.norms.as<float>(),
                      a.argmax.as<int32_t>(), s),
       "pool");
-  p->launches += 5;
+  p->launches += 6;
   return MSS_OK;
 }
 
