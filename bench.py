@@ -235,6 +235,52 @@ def peak_tcups(sms: int, clk_mhz: float) -> float:
     return sms * 4 * 32 * clk_mhz * 1e6 / 1e12
 
 
+def scan_lanes(max_len: int, match: int, mismatch: int, variant: int) -> str:
+    """The 16-bit lanes the scan ran on: f16 x2 (integers up to 2048, exact) when every partial
+    sum fits and both scores have an f16 form with a zero low byte, else int16 x2; a tuned
+    variant (>= 0) decides by itself."""
+    f16_ok = (max_len * match <= 2048 and all(float(np.float16(v)) == v and
+              (int(np.array(v, np.float16).view(np.uint16)) & 0xFF) == 0 for v in (match, mismatch)))
+    v = variant if variant >= 0 else (1 if f16_ok else 0)
+    return "f16x2, exact integers <= 2048" if v == 1 else "int16x2"
+
+
+def bench_line(*, gcups, t, world, args, reads_s, e2e, launches, sms, probe, max_len, wl, genome, lengths,
+               frag_len, tune, tuned, cells_step, scan_ms, cpu, clk) -> dict:
+    """The JSON line of the GPU arm from the measured values (no device work here)."""
+    peak = peak_tcups(sms, 2070.0)
+    # the integer/DPX pipe alone, measured by the library's pipe probe: warp-instructions per
+    # SM clock x 32 threads x 2 lanes / 2 ops per cell, at the same clock
+    dpx_only = probe[0] * 32 * sms * 2070.0e6 / 1e12 if probe else None
+    lanes = scan_lanes(max_len, wl.match, wl.mismatch, tune["variant"])
+    default_run = (wl.name == gen.workloads()[args.workload].name and args.workload == "bact-4.6M"
+                   and args.read_step == 1 and not args.autotune and frag_len == 2048)
+    traffic = SCAN_DRAM_BYTES_DEFAULT if default_run else None
+    scan_mean_ms = statistics.mean(scan_ms)
+    achieved = cells_step / (scan_mean_ms * 1e-3) / 1e12
+    return {
+        "metric": METRIC, "value": round(gcups, 3), "unit": "GCUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(t * 1e3 / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int16", "data": "synthetic",
+        "config": {**workload_config(wl, genome, lengths, frag_len, args, world),
+                   "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
+                   "scan_tune": tune, "autotune": tuned, "scan_lanes": lanes},
+        "reads_per_s": round(reads_s, 1),
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "alu", "kernel": "k_scan (phase-one scan + per-read fragment top-4)",
+                     "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "Tcell/s",
+                     "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "peak_source": f"derived: {sms} SMs x 4 sub-partitions x 32 cells/clk (16-lane integer/DPX "
+                                    "pipe + 16-lane FMA pipe, packed 16-bit x2, 2 ops per cell) x 2070 MHz",
+                     "scan_ms_per_step": round(scan_mean_ms, 3),
+                     "peak_dpx_pipe_only": round(dpx_only, 3) if dpx_only else None,
+                     "frac_of_dpx_pipe_only": round(achieved / dpx_only, 4) if dpx_only else None},
+        "cpu_baseline": cpu,
+        "clocks": clk,
+    }
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -365,44 +411,11 @@ def main():
                "reads_per_s": round(R * e2e_steps * world / te, 1)}
 
     if rank == 0:
-        sms = props.multi_processor_count
-        peak = peak_tcups(sms, 2070.0)
-        # the integer/DPX pipe alone, measured by the library's pipe probe: warp-instructions per
-        # SM clock x 32 threads x 2 lanes / 2 ops per cell, at the same clock
-        dpx_only = probe[0] * 32 * sms * 2070.0e6 / 1e12 if probe else None
-        # the 16-bit lanes the scan ran on: f16 x2 (integers up to 2048, exact) when every partial
-        # sum fits and both scores have an f16 form with a zero low byte, else int16 x2
-        f16_ok = (max_len * wl.match <= 2048 and all(float(np.float16(v)) == v and
-                  (int(np.array(v, np.float16).view(np.uint16)) & 0xFF) == 0 for v in (wl.match, wl.mismatch)))
-        variant = tune["variant"] if tune["variant"] >= 0 else (1 if f16_ok else 0)
-        lanes = "f16x2, exact integers <= 2048" if variant == 1 else "int16x2"
-        default_run = (wl.name == gen.workloads()[args.workload].name and args.workload == "bact-4.6M"
-                       and args.read_step == 1 and not args.autotune and info["frag_len"] == 2048)
-        traffic = SCAN_DRAM_BYTES_DEFAULT if default_run else None
-        scan_mean_ms = statistics.mean(scan_ms)
-        achieved = cells_step / (scan_mean_ms * 1e-3) / 1e12
-        tune = mss.mss_get_tune(g)
-        line = {
-            "metric": METRIC, "value": round(gcups, 3), "unit": "GCUPS", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": round(t * 1e3 / args.steps, 3), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "int16", "data": "synthetic",
-            "config": {**workload_config(wl, genome, lengths, info["frag_len"], args, world),
-                       "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
-                       "scan_tune": tune, "autotune": tuned, "scan_lanes": lanes},
-            "reads_per_s": round(reads_s, 1),
-            "e2e": e2e,
-            "gpu_launches": int(launches),
-            "roofline": {"bound": "alu", "kernel": "k_scan (phase-one scan + per-read fragment top-4)",
-                         "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "Tcell/s",
-                         "frac": round(achieved / peak, 4), "traffic": traffic,
-                         "peak_source": f"derived: {sms} SMs x 4 sub-partitions x 32 cells/clk (16-lane integer/DPX "
-                                        "pipe + 16-lane FMA pipe, packed 16-bit x2, 2 ops per cell) x 2070 MHz",
-                         "scan_ms_per_step": round(scan_mean_ms, 3),
-                         "peak_dpx_pipe_only": round(dpx_only, 3) if dpx_only else None,
-                         "frac_of_dpx_pipe_only": round(achieved / dpx_only, 4) if dpx_only else None},
-            "cpu_baseline": cpu,
-            "clocks": clk,
-        }
+        line = bench_line(
+            gcups=gcups, t=t, world=world, args=args, reads_s=reads_s, e2e=e2e, launches=launches,
+            sms=props.multi_processor_count, probe=probe, max_len=max_len, wl=wl, genome=genome,
+            lengths=lengths, frag_len=info["frag_len"], tune=mss.mss_get_tune(g), tuned=tuned,
+            cells_step=cells_step, scan_ms=scan_ms, cpu=cpu, clk=clk)
         print(json.dumps(line), flush=True)
     g.close()
     if world > 1:
