@@ -35,7 +35,7 @@ constexpr int kTcN = 2 * kTcReads;                    // MMA N: sequences per CT
 constexpr int kTcM = 128;                             // MMA M: fragments per tile
 constexpr uint32_t kTcTile = kTcM * kPropC * 2;       // bytes of a fragment tile (and of a read block)
 constexpr int kTcCap = 256;                           // candidate slots per read
-constexpr int kTcEpiWarps = 4;
+constexpr int kTcEpiWarps = 16;                       // 4 lane quarters x 4 groups of 16 reads
 constexpr int kTcThreads = (kTcEpiWarps + 1) * 32;
 constexpr uint32_t kTcTmemCols = 2 * kTcN;            // two accumulator stages of N columns
 constexpr uint32_t kTcIdesc = idesc_bf16_f32(kTcM, kTcN);
@@ -267,8 +267,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_topk(TcArgs a) {
     }
     __syncwarp();
   } else {
-    // ---- epilogue: strand maximum, threshold, candidate buffers
-    const int frow = 32 * warp + lane;  // fragment row of this thread in a tile
+    // ---- epilogue: warp w reads accumulator lanes 32 (w mod 4) .. + 31 (fragments) and
+    //      columns 32 (w div 4) .. + 31 (16 reads): strand maximum, threshold, candidate buffers
+    const int q = warp & 3, rbase = 16 * (warp >> 2);
+    const int frow = 32 * q + lane;  // fragment row of this thread in a tile
     for (int j = 0; j < nt; ++j) {
       const int s = j & 1;
       // every lane waits (acquire); the tensor-memory loads below need the whole warp
@@ -277,18 +279,31 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_topk(TcArgs a) {
       const int64_t f = (int64_t)(t0 + j) * kTcM + frow;
       if (ok) {
         tc_fence_after();
+        // the reads' thresholds as floats (key 0 accepts every score); rows past the last
+        // fragment take +inf and never pass.  Scores are made canonical (-0 -> +0), so on
+        // them the float order is the key order and "v > threshold" is "key > threshold key".
         const bool fvalid = f < a.NF;
-#pragma unroll 1
-        for (int c = 0; c < kTcN / 32; ++c) {
-          uint32_t x[32];
-          tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(s * kTcN + 32 * c), x);
-          tmem_wait_ld();
+        float th[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const uint32_t k = s_theta[rbase + i];
+          th[i] = !fvalid ? __int_as_float(0x7f800000) : (k == 0u ? __int_as_float(0xff800000) : key_score(k));
+        }
+        uint32_t x[32];
+        tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(s * kTcN + 2 * rbase), x);
+        tmem_wait_ld();
+        float v[16];
+        bool anyp = false;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          v[i] = fmaxf(__uint_as_float(x[2 * i]), __uint_as_float(x[2 * i + 1])) + 0.0f;
+          anyp |= v[i] > th[i];
+        }
+        if (__any_sync(0xffffffffu, anyp)) {
 #pragma unroll
           for (int i = 0; i < 16; ++i) {
-            const int r = 16 * c + i;
-            const float v = fmaxf(__uint_as_float(x[2 * i]), __uint_as_float(x[2 * i + 1]));
-            const uint32_t kv = score_key(v);
-            const bool pred = fvalid && kv > s_theta[r];
+            const int r = rbase + i;
+            const bool pred = v[i] > th[i];
             const uint32_t b = __ballot_sync(0xffffffffu, pred);
             if (b) {
               const int leader = __ffs(b) - 1;
@@ -297,7 +312,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_topk(TcArgs a) {
               basepos = __shfl_sync(0xffffffffu, basepos, leader);
               if (pred) {
                 const int pos = basepos + __popc(b & ((1u << lane) - 1u));
-                s_key[r * kTcCap + pos] = kv;
+                s_key[r * kTcCap + pos] = score_key(v[i]);
                 s_frag[r * kTcCap + pos] = (int32_t)f;
               }
             }
