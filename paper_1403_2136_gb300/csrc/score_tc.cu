@@ -5,13 +5,14 @@
 // accumulation; per read the K best fragments, larger score first, ties -> lower fragment.
 //
 // One CTA = 64 reads (128 sequences: 2i forward, 2i + 1 reverse complement of read i) x a
-// contiguous range of 128-fragment tiles.  Warp 4 (one elected lane) streams the fragment
+// contiguous range of 128-fragment tiles.  Warp 16 (one elected lane) streams the fragment
 // tiles into a two-stage shared-memory ring with bulk copies and issues the MMAs
 // (M = 128 fragments, N = 128 sequences, K = 128, eight K = 16 steps) into one of two
-// tensor-memory accumulator stages.  Warps 0-3 read the accumulators back (thread = fragment,
-// columns = sequences), take the strand maximum, and append every score above the read's
-// current threshold to the read's candidate buffer in shared memory (warp ballot + one
-// shared atomic per read and warp).  When a buffer passes 128 entries the epilogue warps keep
+// tensor-memory accumulator stages.  Sixteen epilogue warps read the accumulators back (warp w:
+// fragment rows 32 (w mod 4) .. + 31, the 16 reads 16 (w div 4) .. + 15), take the strand
+// maximum, and append every score above the read's current threshold to the read's candidate
+// buffer in shared memory (one warp vote per tile, then a ballot + one shared atomic per read
+// that has a passing score).  When a buffer passes 128 entries the epilogue warps keep
 // its K best (warp-wide selection of the K-th largest key) and raise the threshold.  Tiles
 // are processed in increasing fragment order, so a later fragment equal to the threshold
 // loses the tie and is never appended.  With several CTAs per read block (fragment splits)
@@ -293,29 +294,31 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_topk(TcArgs a) {
         tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(s * kTcN + 2 * rbase), x);
         tmem_wait_ld();
         float v[16];
-        bool anyp = false;
+        uint32_t m = 0u;  // bit i: this thread's score for read rbase + i passes
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
           v[i] = fmaxf(__uint_as_float(x[2 * i]), __uint_as_float(x[2 * i + 1])) + 0.0f;
-          anyp |= v[i] > th[i];
+          m |= (v[i] > th[i] ? 1u : 0u) << i;
         }
-        if (__any_sync(0xffffffffu, anyp)) {
+        // append, read by read, only for the reads where some lane passes
+        uint32_t mm = __reduce_or_sync(0xffffffffu, m);
+        while (mm) {
+          const int i = __ffs(mm) - 1;
+          mm &= mm - 1u;
+          const int r = rbase + i;
+          const bool pred = (m >> i) & 1u;
+          const uint32_t b = __ballot_sync(0xffffffffu, pred);
+          const int leader = __ffs(b) - 1;
+          int basepos = 0;
+          if (lane == leader) basepos = atomicAdd(&s_cnt[r], __popc(b));
+          basepos = __shfl_sync(0xffffffffu, basepos, leader);
+          if (pred) {
+            float vi = v[0];
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const int r = rbase + i;
-            const bool pred = v[i] > th[i];
-            const uint32_t b = __ballot_sync(0xffffffffu, pred);
-            if (b) {
-              const int leader = __ffs(b) - 1;
-              int basepos = 0;
-              if (lane == leader) basepos = atomicAdd(&s_cnt[r], __popc(b));
-              basepos = __shfl_sync(0xffffffffu, basepos, leader);
-              if (pred) {
-                const int pos = basepos + __popc(b & ((1u << lane) - 1u));
-                s_key[r * kTcCap + pos] = score_key(v[i]);
-                s_frag[r * kTcCap + pos] = (int32_t)f;
-              }
-            }
+            for (int k = 1; k < 16; ++k) vi = (k == i) ? v[k] : vi;
+            const int pos = basepos + __popc(b & ((1u << lane) - 1u));
+            s_key[r * kTcCap + pos] = score_key(vi);
+            s_frag[r * kTcCap + pos] = (int32_t)f;
           }
         }
       }
