@@ -196,6 +196,46 @@ def test_errors_are_reported(mss):
     g.close()
 
 
+def test_empty_batches_and_empty_reads(mss):
+    """R = 0 is a no-op on every entry point; a read of length 0 is rejected with
+    MSS_EREADLEN (host calls: before any launch; device calls: by the length check of the
+    ordering kernel, reported at the next synchronisation) and the context stays usable."""
+    import torch
+    rng = np.random.default_rng(9)
+    genome = rng.choice(np.frombuffer(b"ACGT", np.uint8), size=5000).tobytes()
+    g = mss.mss_load_genome(genome, frag_len=500, max_read_len=200)
+    seq, off = concat_reads([])
+    assert mss.mss_map_reads(g, seq, off, 5, -4).shape == (0,)
+    alns, cigs = mss.nw_align(g, seq, off, np.zeros(0, dtype=mss.HIT_DTYPE), 5, -4, -10, -1, 32)
+    assert alns.shape == (0,) and cigs == []
+    hits, alns, _ = mss.mss_map_align(g, seq, off, 5, -4, (5, -4, -10, -1, 32))
+    assert hits.shape == (0,) and alns.shape == (0,)
+    d_seq = torch.zeros(16, dtype=torch.uint8, device="cuda")
+    d_off = torch.zeros(1, dtype=torch.int64, device="cuda")
+    d_hits = torch.zeros(32, dtype=torch.uint8, device="cuda")
+    mss.mss_map_reads_device(g, d_seq, d_off, 0, 1, 5, -4, d_hits)
+    mss.mss_sync(g)
+
+    reads = [genome[100:200], b"", genome[300:350]]
+    seq, off = concat_reads(reads)
+    with pytest.raises(mss.MssError) as e:
+        mss.mss_map_reads(g, seq, off, 5, -4)
+    assert e.value.status == mss.MSS_EREADLEN
+    d_seq, d_off = torch.from_numpy(seq).cuda(), torch.from_numpy(off).cuda()
+    d_hits = torch.zeros(3 * 32, dtype=torch.uint8, device="cuda")
+    mss.mss_map_reads_device(g, d_seq, d_off, 3, 100, 5, -4, d_hits)
+    with pytest.raises(mss.MssError) as e:
+        mss.mss_sync(g)
+    assert e.value.status == mss.MSS_EREADLEN
+    # the context stays usable and the next call is exact
+    seq, off = concat_reads([genome[100:200], genome[300:350]])
+    hits, _, _, oh, _, _ = run_both(mss, genome, seq, off, 500, 5, -4, max_len=200, procs=1)
+    assert_hits_equal(hits, oh, "after an empty-read error")
+    h = mss.mss_map_reads(g, seq, off, 5, -4)
+    assert list(h["best_score"]) == [500, 250]
+    g.close()
+
+
 def test_autotune_keeps_results(mss):
     import torch
     wl = gen.scaled(gen.workloads()["bact-4.6M"], genome_len=80_000, reads=48)
