@@ -53,7 +53,9 @@ def _lib():
     global _LIB
     with _LOCK:
         if _LIB is None:
-            lib = ctypes.CDLL(build())
+            # MSS_ORACLE_LIB: a compiled variant of oracle.c to load instead (the tests that plant
+            # mistakes in the oracle use it to show that the pins catch them)
+            lib = ctypes.CDLL(os.environ.get("MSS_ORACLE_LIB") or build())
             P = ctypes.c_void_p
             i32, i64 = ctypes.c_int32, ctypes.c_int64
             lib.orc_base_code.argtypes = [ctypes.c_int]

@@ -280,6 +280,33 @@ def test_ratio_flag_integer_form():
         assert h[6] == (1 if (b == 0 or s / b >= 0.9) else 0)
 
 
+def test_lowercase_bases_are_bases():
+    """Either case codes the same base (the genome and the reads may be soft-masked)."""
+    assert list(oracle.encode("acgtn")) == list(oracle.encode("ACGTN")) == [0, 1, 2, 3, 4]
+    rng = np.random.default_rng(22)
+    genome = "".join(rng.choice(list("ACGT"), size=600))
+    read = genome[210:250]
+    up = oracle.map_read(genome, 100, read, 5, -4)
+    assert up[2] == 200
+    assert oracle.map_read(genome.lower(), 100, read.lower(), 5, -4) == up
+    assert oracle.map_read(genome, 100, read[:20].lower() + read[20:], 5, -4) == up
+
+
+def test_ratio_flag_boundary_is_inclusive():
+    """second / best exactly 0.9 is not "below .9": the read is a repeat.  An exact 10-base
+    copy (5 * 10 = 50) and a copy with its last base changed (the run of 9 scores 45)."""
+    rng = np.random.default_rng(21)
+    gen = list("".join(rng.choice(list("ACGT"), size=2000)))
+    read = "ACGTTGCAAC"
+    gen[150:160] = list(read)
+    gen[1250:1260] = list(read[:9] + "A")
+    h = oracle.map_read("".join(gen), 100, read, 5, -4)
+    assert h[:4] == (1, 12, 50, 45) and h[6] == 1
+    gen[1250:1260] = list(read[:8] + "GA")          # a run of 8: 40 / 50 = 0.8, mapped
+    h = oracle.map_read("".join(gen), 100, read, 5, -4)
+    assert h[2] == 50 and h[3] < 45 and h[6] == 0
+
+
 # ---------------------------------------------------------------- Figure 2 toy genome
 def _golden(name):
     d = {}
@@ -427,6 +454,22 @@ def test_nw_banded_equals_unbanded_when_optimum_in_band():
         a = oracle.nw_banded(g, q, d, 32, 5, -4, -10, -1)
         b = oracle.nw_banded(g, q, d, 400, 5, -4, -10, -1)
         assert a == b
+
+
+def test_nw_band_edges_are_inclusive():
+    """The band is |t| <= W for t = column - row - seed offset: a deletion of exactly W bases
+    (t = +W after it) or an insertion of W bases (t = -W) still aligns inside band W, with
+    the unbanded result; band W - 1 cannot reach it."""
+    rng = np.random.default_rng(21)
+    genome = "".join(rng.choice(list("ACGT"), size=400))
+    g = oracle.encode(genome)
+    W = 4
+    for read, op in ((genome[100:140] + genome[140 + W:180 + W], "4D"), (genome[100:140] + "TTGA" + genome[140:180], "4I")):
+        q = oracle.encode(read)
+        inside = oracle.nw_banded(g, q, 100, W, 5, -4, -10, -1)
+        assert inside == oracle.nw_banded(g, q, 100, 400, 5, -4, -10, -1)
+        assert inside[0] == 80 * 5 - 10 - 3 and inside[3] == "40M" + op + "40M"
+        assert oracle.nw_banded(g, q, 100, W - 1, 5, -4, -10, -1)[0] < inside[0]
 
 
 def test_nw_literal_region():

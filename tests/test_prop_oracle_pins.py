@@ -1,9 +1,17 @@
 """Pins of the proposal-network oracle (no GPU): the backward pass against finite
 differences of the forward pass, the loss gradient against finite differences, and the
 defining properties of the forward pass (unit norm, padding invariance, N = zero input)."""
+import importlib.util
+import os
+
 import numpy as np
 
-from oracle import prop_oracle as po
+if os.environ.get("MSS_PROP_ORACLE"):   # a variant with a planted mistake (tests/test_oracle_mutants.py)
+    _spec = importlib.util.spec_from_file_location("prop_oracle_variant", os.environ["MSS_PROP_ORACLE"])
+    po = importlib.util.module_from_spec(_spec)
+    _spec.loader.exec_module(po)
+else:
+    from oracle import prop_oracle as po
 
 
 def small_params(seed=0, scale=0.2):
@@ -77,3 +85,61 @@ def test_bf16_rounding_ties_to_even():
     # 1 + 2^-8 is halfway between 1 and 1 + 2^-7: ties go to the even mantissa (1.0)
     assert po.bf16_round(np.array([1.0 + 2 ** -8]))[0] == 1.0
     assert po.bf16_round(np.array([1.0 + 3 * 2 ** -8]))[0] == 1.0 + 2 ** -6
+
+
+def _one_path_params(w1v, wv, taps):
+    """Every weight zero except one path: channel 0 of layer 1 reads base A through tap
+    taps[0], and layer l (2..4) passes channel 0 on through tap taps[l - 1]; biases zero."""
+    p = np.zeros(po.param_count())
+    p[(taps[0] * 4 + 0) * po.C + 0] = w1v
+    o = po.TAPS * 4 * po.C + po.C
+    for l in range(3):
+        p[o + (taps[l + 1] * po.C + 0) * po.C + 0] = wv[l]
+        o += po.TAPS * po.C * po.C + po.C
+    return p
+
+
+def test_forward_fixed_by_hand():
+    """The forward pass on a one-path network, worked out by hand: tap t at position p reads
+    position p + t - 3 (zero outside the sequence), the max pool keeps the first maximum,
+    the embedding is v / (|v| + 1e-6), and the stored values follow the rounding points
+    (layer outputs rounded to BF16; layers 2-4 use BF16 weights, layer 1 FP32 ones)."""
+    codes = np.array([1, 2, 0, 3, 1, 0, 2, 2, 1, 3, 3, 1, 0, 2])   # A at 2, 5 and 12; L = 14
+    p = _one_path_params(1 + 2 ** -9, (1 + 2 ** -7, 1 + 2 ** -9, 1 + 2 ** -7), taps=(0, 0, 3, 3))
+    e, (_, _, arg, v, nrm) = po.forward(p, codes)
+    # two taps 0: position p sees base p - 6.  The A at 2 and 5 fire at 8 and 11 with equal
+    # values (the first is kept); the A at 12 would fire at 18, outside the sequence.
+    assert arg[0] == 8
+    # bf16(1 + 2^-9) = 1 (layer 1 output); x (1 + 2^-7) exact; weight 1 + 2^-9 -> 1;
+    # x (1 + 2^-7): 1 + 2^-6 + 2^-14 -> 1 + 2^-6
+    assert v[0] == 1 + 2 ** -6 and np.all(v[1:] == 0)
+    assert nrm == v[0] + 1e-6 and e[0] == v[0] / (v[0] + 1e-6) and np.all(e[1:] == 0)
+    _, (_, _, arg_x, v_x, _) = po.forward(p, codes, rounding=False)
+    assert arg_x[0] == 8 and abs(v_x[0] - (1 + 2 ** -9) ** 2 * (1 + 2 ** -7) ** 2) < 1e-12
+    # values that cross rounding boundaries (BF16 steps of 2^-7 in [1, 2)), w = 1 + 2^-8 + 2^-9:
+    # layer 1 (FP32 weight w): bf16(w) = 1 + 2^-7; layer 2 (x 1.75): 1.763671875 -> 1.765625;
+    # layer 3 (BF16 weight bf16(w) = 1 + 2^-7): 1.779418... -> 1.78125; layer 4 x 1.
+    # Skipping the layer-1 rounding would give 1.7578125 after layer 2, an FP32 layer-3
+    # weight 1.7734375 after layer 3.
+    w = 1 + 2 ** -8 + 2 ** -9
+    p = _one_path_params(w, (1.75, w, 1.0), taps=(0, 0, 3, 3))
+    _, (_, _, arg, v, _) = po.forward(p, codes)
+    assert arg[0] == 8 and v[0] == 1.78125
+    # two taps 6: position p sees base p + 6; only the A at 12 lands inside (at 6)
+    p = _one_path_params(1.0, (1.0, 1.0, 1.0), taps=(6, 6, 3, 3))
+    e, (_, _, arg, v, _) = po.forward(p, codes)
+    assert arg[0] == 6 and v[0] == 1.0
+    # N is no base: with the A at 12 replaced by N nothing fires and the embedding is zero
+    codes_n = codes.copy()
+    codes_n[12] = 4
+    e, (_, _, _, v, nrm) = po.forward(p, codes_n)
+    assert np.all(v == 0) and nrm == 1e-6 and np.all(e == 0)
+    # T (code 3) is a base like the others: a T-reading path fires on the T at 3
+    q = np.zeros(po.param_count())
+    q[(3 * 4 + 3) * po.C + 0] = 1.0                       # layer 1, tap 3 (the position itself), base T
+    o = po.TAPS * 4 * po.C + po.C
+    for _ in range(3):
+        q[o + (3 * po.C + 0) * po.C + 0] = 1.0
+        o += po.TAPS * po.C * po.C + po.C
+    _, (_, _, arg, v, _) = po.forward(q, codes)
+    assert arg[0] == 3 and v[0] == 1.0
