@@ -8,18 +8,18 @@
 // copied into shared memory once and stay there.  Work item = 128 positions of one sequence;
 // even CTAs take the low half and odd CTAs the high half of the same items, so the partner's
 // read of an input tile hits L2.  Roles, linked only by mbarriers:
-//   warp 0  producer: per item 16 TMA tensor copies (one per 8-channel group, 134 rows x 16 B)
-//           into a three-stage ring of input tiles;
+//   warp 0  producer: per item two TMA tensor copies (channels 0-63 and 64-127, 134 rows of
+//           128 B each) into a three-stage ring of input tiles;
 //   warp 1  one thread issues the item's 56 MMAs (7 taps x 8 K-steps of M = 128, N = 64,
 //           K = 16, BF16 -> FP32) into one of three 64-column tensor-memory accumulators;
 //   warps 2-5  epilogue: tcgen05.ld of the accumulator (warp w reads lanes 32 (w mod 4) .. + 31),
 //           release it, then bias + ReLU + mask and the BF16 store.
-// The input tile is "k-group major": the group g of channels 8g .. 8g+7 of row r sits at
-// g * 2176 + r * 16 (136-row groups, so every TMA destination is 128-byte aligned).  That is
-// the canonical K-major operand layout without swizzling, with a stride-dimension offset of
-// 128 bytes (8 rows) and a leading-dimension offset of one group, and the tap shift becomes a
-// start-address offset of t * 16 bytes: the A operand of tap t is rows t .. t + 127.  Every
-// wait is time-bounded and reports through the error word.
+// Each half of an input tile is K-major in the 128-byte swizzled layout (rows of 128 B in
+// 1 KB atoms of 8 rows, written swizzled by the TMA unit), so a K-step is a 32-byte start
+// offset inside a row and the tap shift is a start offset of t rows (t * 128 B); one staged
+// tile serves all 7 taps.  The resident weights use the
+// canonical K-major layout without swizzling.  Every wait is time-bounded and reports through
+// the error word.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -41,8 +41,8 @@ constexpr int kCtM = 128;                              // positions per item
 constexpr int kCtN = 64;                               // output channels per CTA
 constexpr int kCtRows = kCtM + 6;                      // with the halo
 constexpr int kCtStages = 3;
-constexpr uint32_t kCtGroupA = 136 * 16;               // one channel group of an input tile
-constexpr uint32_t kCtBytesA = 16 * kCtGroupA;         // 34,816 per stage
+constexpr uint32_t kCtHalfA = 17 * 1024;               // 64 channels x 134 rows of 128 B, whole 1 KB atoms
+constexpr uint32_t kCtBytesA = 2 * kCtHalfA;           // 34,816 per stage
 constexpr uint32_t kCtTxA = 16 * kCtRows * 16;         // 34,304 bytes land per item
 constexpr uint32_t kCtGroupW = kCtN * 16;              // one channel group of a tap's half weights
 constexpr uint32_t kCtTapW = 16 * kCtGroupW;           // 16,384 per tap and half
@@ -56,7 +56,24 @@ constexpr uint32_t kCtIdesc = idesc_bf16_f32(kCtM, kCtN);
 constexpr uint64_t kCtWaitNs = 2000000000ull;
 static_assert(kCtSmem + 1024 <= 227 * 1024, "shared memory of the conv CTA");
 static_assert(kCtStages * kCtN <= (int)kCtTmemCols, "tensor-memory columns");
-static_assert(kCtOffW % 1024 == 0 && kCtGroupA % 128 == 0, "operand alignment");
+static_assert(kCtOffW % 1024 == 0 && kCtHalfA % 1024 == 0 && kCtBytesA % 1024 == 0, "operand alignment");
+static_assert(kCtRows * 128 <= (int)kCtHalfA, "input tile half");
+
+// Shared-memory descriptor of a K-major operand in the 128-byte swizzled layout (rows of 128 B,
+// 8-row atoms of 1 KB, the 16-byte chunks of row r XOR-ed with r mod 8, as the TMA unit writes
+// them with CU_TENSOR_MAP_SWIZZLE_128B into 1 KB-aligned buffers): stride-dimension offset
+// 1 KB, layout type 2 (bits 61-63), base offset 0.  The swizzle follows the absolute address
+// bits, so a start moved by whole 128-byte rows (the tap shift) or by 32 bytes inside a row
+// (a K-step) reads the tile as written (checked against the oracle by the embedding and
+// gradient tests).
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;                      // leading-dimension offset (unused for this layout)
+  d |= (uint64_t)(1024 >> 4) << 32;            // stride-dimension offset: 8 rows
+  d |= (uint64_t)1 << 46;                      // version
+  d |= (uint64_t)2 << 61;                      // 128-byte swizzle
+  return d;
+}
 
 // 2-D tiled TMA load of box (x .. x + 7 channels, y .. y + 133 rows) completing on bar
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int32_t x, int32_t y,
@@ -140,7 +157,7 @@ __global__ void __launch_bounds__(kCtThreads, 1) k_conv_tc(const __grid_constant
           mbar_arrive_expect_tx(&afull[s], kCtTxA);
           const int32_t y = it.n * rows + it.p0;  // padded row of position p0 - 3
 #pragma unroll
-          for (int g = 0; g < 16; ++g) tma_load_2d(sA + s * kCtBytesA + g * kCtGroupA, &tin, 8 * g, y, &afull[s]);
+          for (int h = 0; h < 2; ++h) tma_load_2d(sA + s * kCtBytesA + h * kCtHalfA, &tin, 64 * h, y, &afull[s]);
         } else {
           mbar_arrive(&afull[s]);
         }
@@ -162,7 +179,7 @@ __global__ void __launch_bounds__(kCtThreads, 1) k_conv_tc(const __grid_constant
           for (int t = 0; t < kPropTaps; ++t) {
 #pragma unroll
             for (int ks = 0; ks < kPropC / 16; ++ks)
-              tc_mma_bf16(d, smem_desc(a0 + (2 * ks) * kCtGroupA + t * 16, kCtGroupA, 128),
+              tc_mma_bf16(d, smem_desc_sw128(a0 + (ks >> 2) * kCtHalfA + t * 128 + (ks & 3) * 32),
                           smem_desc(sW + t * kCtTapW + (2 * ks) * kCtGroupW, kCtGroupW, 128), kCtIdesc,
                           (t > 0 || ks > 0) ? 1u : 0u);
           }
@@ -300,10 +317,10 @@ cudaError_t prop_conv_tc(const __nv_bfloat16* in, const void* wcanon, const floa
   CUtensorMap map;
   const cuuint64_t dims[2] = {(cuuint64_t)kPropC, (cuuint64_t)n * rows};
   const cuuint64_t strides[1] = {(cuuint64_t)kPropC * sizeof(__nv_bfloat16)};
-  const cuuint32_t box[2] = {8, (cuuint32_t)kCtRows};
+  const cuuint32_t box[2] = {64, (cuuint32_t)kCtRows};
   const cuuint32_t estr[2] = {1, 1};
   if (encode(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(in), dims, strides, box, estr,
-             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return cudaErrorInvalidValue;
   // one CTA per SM, an even count (the two output halves of an item go to CTAs 2i and 2i + 1)
