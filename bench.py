@@ -158,7 +158,9 @@ def run_reference(args):
             tot_reads += r
             tot_t += dt
     gcups = tot_cells / tot_t / 1e9
-    sample = (f"{cores} reads per step (one per core, evenly spaced over the workload's 100/150 bp reads), "
+    lens = sorted(set(np.diff(off).tolist()))
+    span = f"{lens[0]}-{lens[-1]} bp" if len(lens) > 3 else "/".join(str(x) for x in lens) + " bp"
+    sample = (f"{cores} reads per step (one per core, evenly spaced over the workload's {span} reads), "
               f"phase one + banded NW")
     line = {
         "impl": "reference", "metric": METRIC, "value": round(gcups, 4), "unit": "GCUPS", "n_gpus": args.gpus,
