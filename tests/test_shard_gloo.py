@@ -42,6 +42,24 @@ def test_merge_equals_whole_genome(world):
     assert_hits_equal(got, want, f"{world} shards")
 
 
+@pytest.mark.parametrize("genome_len,world", [(4_500, 4), (4_500, 7), (900, 3)])
+def test_merge_with_ranks_that_own_no_fragment(genome_len, world):
+    """More ranks than fragments (or a rank left over by the rounding of the split): the
+    empty ranks contribute empty records and the merge still equals the whole genome; with a
+    single fragment the merged second is -1 with score 0."""
+    wl = gen.scaled(gen.workloads()["bact-4.6M"], genome_len=genome_len, reads=16)
+    genome, reads = gen.materialize(wl)
+    F, ml = 1000, int(np.diff(reads.offsets).max())
+    bounds = [shard.shard_bounds(genome.shape[0], F, world, r, ml) for r in range(world)]
+    assert any(f1 <= f0 for f0, f1, _, _ in bounds)           # some rank owns nothing
+    recs = [_oracle_shard(genome, F, reads, 5, -4, world, r, ml) for r in range(world)]
+    got = shard.records_to_hits(shard.merge(recs))
+    want, _, _ = oracle.map_batch(genome, F, reads.seq, reads.offsets, 5, -4)
+    assert_hits_equal(got, want, f"{world} shards of {genome_len} bp")
+    if genome_len <= F:
+        assert np.all(got["second_frag"] == -1) and np.all(got["second_score"] == 0)
+
+
 def _free_port():
     s = socket.socket()
     s.bind(("127.0.0.1", 0))
