@@ -261,7 +261,8 @@ typedef struct mss_prop mss_prop;
 MSS_API mss_status mss_prop_create(mss_prop** out, uint64_t seed, void* stream);
 MSS_API void mss_prop_free(mss_prop* p);
 /* Number of parameters and the flat fp32 layout: W1 [7][4][128], b1 [128], then for layers
-   2..4: W [7][128 in][128 out], b [128].  get/set copy host <-> device. */
+   2..4: W [7][128 in][128 out], b [128].  get/set copy host <-> device; n must equal
+   mss_prop_param_count() (else MSS_EINVAL). */
 MSS_API int64_t mss_prop_param_count(void);
 MSS_API mss_status mss_prop_get_params(const mss_prop* p, float* host, int64_t n);
 MSS_API mss_status mss_prop_set_params(mss_prop* p, const float* host, int64_t n);
@@ -273,7 +274,9 @@ MSS_API mss_status mss_prop_read_codes(mss_prop* p, const char* d_reads, const i
                                        uint8_t* d_codes, int32_t* d_lens, void* stream);
 MSS_API mss_status mss_prop_window_codes(mss_prop* p, const mss_ctx* ctx, const int64_t* d_starts, int32_t n,
                                          int32_t len, int32_t ld, uint8_t* d_codes, int32_t* d_lens, void* stream);
-/* Embeddings of n code sequences (lengths <= maxlen <= ld) into d_emb [n][128] (fp32). */
+/* Embeddings of n code sequences (lengths <= maxlen <= ld) into d_emb [n][128] (fp32).
+   MSS_EINVAL for n < 0 or maxlen outside [1, ld]; MSS_ETIMEOUT if a bounded wait of a
+   tensor-core kernel gave up (the model stays usable). */
 MSS_API mss_status mss_prop_embed_device(mss_prop* p, const uint8_t* d_codes, const int32_t* d_lens, int32_t ld,
                                          int32_t n, int32_t maxlen, float* d_emb, void* stream);
 /* Parameter gradient (d_grad, mss_prop_param_count() floats) of sum_i <d_demb[i], emb_i>. */
@@ -281,23 +284,31 @@ MSS_API mss_status mss_prop_grad_device(mss_prop* p, const uint8_t* d_codes, con
                                         int32_t n, int32_t maxlen, const float* d_demb, float* d_grad, void* stream);
 /* One training step: B read sequences (on their labelled strand) against C candidate
    fragment windows; label[i] = index of read i's best fragment among the candidates; loss =
-   mean softmax cross-entropy of <e_read, e_cand> / temperature.  loss_out (host) optional. */
+   mean softmax cross-entropy of <e_read, e_cand> / temperature.  loss_out (host) optional.
+   MSS_EINVAL unless B >= 1, 2 <= C <= 1024, lr > 0 and temperature > 0. */
 MSS_API mss_status mss_prop_train_step(mss_prop* p, const uint8_t* d_rcodes, const int32_t* d_rlens, int32_t ld_r,
                                        int32_t B, int32_t maxlen_r, const uint8_t* d_ccodes, const int32_t* d_clens,
                                        int32_t ld_c, int32_t C, int32_t maxlen_c, const int32_t* d_labels, float lr,
                                        float temperature, float weight_decay, float* loss_out, void* stream);
-/* Embed every fragment window [fF, fF + F + max_read_len - 1) of the context's genome. */
+/* Embed every fragment window [fF, fF + F + max_read_len - 1) of the context's genome.
+   MSS_EREADLEN for max_read_len outside [1, the context's maximum]; MSS_EINVAL for a window
+   above 65,536 bases. */
 MSS_API mss_status mss_prop_build_index(mss_prop* p, mss_ctx* ctx, int32_t max_read_len, void* stream);
 /* Proposal + exact rescoring: per read the top K fragments by embedding score (ties -> lower
    fragment), the exact scan of those K (both strands), and best / second among them; reads
    whose best proposal score is below tau are mapped by the exhaustive scan instead.  Optional
    outputs: d_cand [R][K] candidate fragments, d_top_score [R] best proposal score,
-   *n_fallback (host) the number of fallback reads.  Synchronous. */
+   *n_fallback (host) the number of fallback reads.  Synchronous.  MSS_ESTATE when no index
+   was built for this context's genome or the fragment length changed since; MSS_EINVAL for
+   K outside [1, 1024] or bad scores; MSS_EREADLEN for max_len outside [1, the context's
+   maximum]. */
 MSS_API mss_status mss_map_reads_proposed(mss_ctx* ctx, mss_prop* p, const char* d_reads, const int64_t* d_offsets,
                                           int32_t R, int32_t max_len, const mss_score_params* sp, int32_t K,
                                           float tau, mss_hit* d_out, int32_t* d_cand, float* d_top_score,
                                           int32_t* n_fallback, void* stream);
-/* Checkpoint: master weights and Adam state in a flat file with a header and a CRC-32. */
+/* Checkpoint: master weights and Adam state in a flat file with a header and a CRC-32.
+   mss_prop_load rejects (MSS_EINVAL, model unchanged) a file with another header or size, a
+   truncated file or a CRC mismatch. */
 MSS_API mss_status mss_prop_save(const mss_prop* p, const char* path);
 MSS_API mss_status mss_prop_load(mss_prop* p, const char* path);
 MSS_API int64_t mss_prop_launch_count(const mss_prop* p);
