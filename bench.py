@@ -3,10 +3,12 @@
 
 One step = the whole hot path over one batch: phase one (exact MSS scan of every read on
 both strands along every genome diagonal, per-fragment maxima, top-2 fragments, best-diagonal
-rescan) and phase two (banded NW) for every read of the workload.  Default workload: the
+rescan) and phase two (banded NW) for every read of the batch.  Default workload: the
 bacterial-genome shape, a 4.6 Mbp synthetic genome (GC 50.8%, 2% exact 1-5 kbp repeat
 copies), F = 2048, 200,000 reads of 100 bp and 200,000 of 150 bp at 10/20/30% substitutions
-with up to two geometric gaps <= 30 bp, scores 5/-4, banded NW 5/-4/-10/-1 with W = 32.
+with up to two geometric gaps <= 30 bp, scores 5/-4, banded NW 5/-4/-10/-1 with W = 32.  The
+400,000 reads are dealt into batches of 50,000 (read b, b + 8, b + 16, ...: every batch has
+the same mix) and the steps cycle through the batches.
 
 Metric: GCUPS = sum over reads of m * Gp * 2 strands / step time (the paper reports
 wall-clock minutes; cells per second is the standard unit of alignment scans), and reads/s.
@@ -50,6 +52,7 @@ def parse():
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--workload", default="bact-4.6M")
     ap.add_argument("--reads", type=int, default=0, help="override the read count (testing only)")
+    ap.add_argument("--batch", type=int, default=50_000, help="reads per step (the workload is dealt into batches)")
     ap.add_argument("--genome", type=int, default=0, help="override the genome length (testing only)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -66,28 +69,42 @@ def workload(args, rank: int):
     wl = gen.workloads()[args.workload]
     if args.reads or args.genome:
         wl = gen.scaled(wl, genome_len=args.genome or None, reads=args.reads or None)
-    wl.seed = wl.seed  # genome identical on every rank; reads drawn per rank below
-    genome = gen.make_genome(wl.genome, wl.seed)
-    parts = [gen.make_reads(genome, rs, wl.seed * 31 + i + 1000003 * rank) for i, rs in enumerate(wl.reads)]
-    seq = np.concatenate([p.seq for p in parts])
-    lens = np.concatenate([p.lengths for p in parts]).astype(np.int64)
-    off = np.zeros(lens.shape[0] + 1, dtype=np.int64)
-    np.cumsum(lens, out=off[1:])
-    return wl, genome, seq, off
+    genome = gen.make_genome(wl.genome, wl.seed)      # identical on every rank
+    reads = gen.read_set(wl, genome, rank)             # reads drawn per rank
+    return wl, genome, reads.seq, reads.offsets
 
 
-# DRAM bytes (read + write) of one k_scan launch of the default workload (bact-4.6M, all
-# 400,000 reads, F = 2048, read step 1), from one ncu capture of that launch with
-# dram__bytes_read.sum and dram__bytes_write.sum (one pass); the capture and its command are in
-# profiles/launches_bact-4.6M_400k-reads.md.  Other workloads report no traffic.
-SCAN_DRAM_BYTES_DEFAULT = 60.29e6
+def batches(seq, off, batch: int):
+    """The workload dealt into ceil(R / batch) batches of equal mix: (seq, offsets) per batch."""
+    R = off.shape[0] - 1
+    nb = max(1, -(-R // max(1, batch)))
+    out = []
+    for b in range(nb):
+        idx = gen.batch_index(R, nb, b)
+        lens = (off[idx + 1] - off[idx]).astype(np.int64)
+        o = np.zeros(idx.shape[0] + 1, dtype=np.int64)
+        np.cumsum(lens, out=o[1:])
+        starts = np.repeat(off[idx] - o[:-1], lens)
+        s = seq[np.arange(o[-1], dtype=np.int64) + starts]
+        out.append((s, o))
+    return out
+
+
+# DRAM bytes (read + write) of one k_scan launch of the default workload (bact-4.6M, one
+# 50,000-read batch, F = 2048, read step 1), from an ncu capture of that launch with
+# dram__bytes_read.sum and dram__bytes_write.sum (one pass); None until captured for the
+# kernel as built.  Other workloads report no traffic.
+SCAN_DRAM_BYTES_DEFAULT = None
 
 
 def workload_config(wl, genome, lengths, F: int, args, world: int = 1) -> dict:
     """The `config` object both arms report for the same workload."""
     Gp = -(-int(genome.shape[0]) // F) * F
+    R = int(lengths.shape[0])
+    nb = max(1, -(-R // max(1, args.batch)))
     return {"workload": wl.name, "genome_bp": int(genome.shape[0]), "frag_len": F, "padded_bp": Gp,
-            "reads": int(lengths.shape[0]), "read_lengths": sorted(set(np.asarray(lengths).tolist())),
+            "reads": R, "batch_reads": -(-R // nb), "batches": nb,
+            "read_lengths": sorted(set(np.asarray(lengths).tolist())),
             "scores": [wl.match, wl.mismatch], "nw": list(wl.nw),
             "parallelism": f"replicas x{world} (read batches per GPU)", "read_step": args.read_step}
 
@@ -230,11 +247,21 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------- GPU arm
-def peak_tcups(sms: int, clk_mhz: float) -> float:
-    """Roofline of the scan: 2 int16 ops per cell (add-relu, max); packed 16-bit x2 work runs on
-    two pipes of 16 lanes per SM sub-partition each (integer/DPX pipe and FMA pipe), so at most
+def peak_nominal_tcups(sms: int, clk_mhz: float) -> float:
+    """Nominal two-pipe figure: 2 int16 ops per cell (add-relu, max); packed 16-bit x2 work runs
+    on two pipes of 16 lanes per SM sub-partition each (integer/DPX and FMA), so at most
     2 pipes x 16 lanes x 2 halves / 2 ops = 32 cells per clock per sub-partition, 4 per SM."""
     return sms * 4 * 32 * clk_mhz * 1e6 / 1e12
+
+
+def peak_measured_tcups(probe, sms: int, clk_mhz: float):
+    """Measured two-pipe figure: the library's pipe probe with one packed int16 DPX add-max and
+    one packed f16 FMA-relu per chain step (both pipes busy) gives warp-instructions per SM
+    clock; each packed warp-instruction is 64 lane operations, a cell needs 2, so cells per SM
+    clock = rate x 32."""
+    if not probe:
+        return None
+    return probe[2] * 32 * sms * clk_mhz * 1e6 / 1e12
 
 
 def scan_lanes(max_len: int, match: int, mismatch: int, variant: int) -> str:
@@ -248,22 +275,30 @@ def scan_lanes(max_len: int, match: int, mismatch: int, variant: int) -> str:
 
 
 def bench_line(*, gcups, t, world, args, reads_s, e2e, launches, sms, probe, max_len, wl, genome, lengths,
-               frag_len, tune, tuned, cells_step, scan_ms, cpu, clk) -> dict:
+               frag_len, tune, tuned, cells_timed, scan_ms, cpu, clk) -> dict:
     """The JSON line of the GPU arm from the measured values (no device work here)."""
-    peak = peak_tcups(sms, 2070.0)
-    # the integer/DPX pipe alone, measured by the library's pipe probe: warp-instructions per
-    # SM clock x 32 threads x 2 lanes / 2 ops per cell, at the same clock
-    dpx_only = probe[0] * 32 * sms * 2070.0e6 / 1e12 if probe else None
+    clk_mhz = 2070.0
+    nominal = peak_nominal_tcups(sms, clk_mhz)
+    measured = peak_measured_tcups(probe, sms, clk_mhz)
+    peak = measured if measured else nominal
+    # the integer/DPX pipe alone, measured by the same probe: warp-instructions per SM clock x
+    # 32 threads x 2 lanes / 2 ops per cell
+    dpx_only = probe[0] * 32 * sms * clk_mhz * 1e6 / 1e12 if probe else None
     lanes = scan_lanes(max_len, wl.match, wl.mismatch, tune["variant"])
     default_run = (wl.name == gen.workloads()[args.workload].name and args.workload == "bact-4.6M"
-                   and args.read_step == 1 and not args.autotune and frag_len == 2048)
+                   and args.read_step == 1 and not args.autotune and frag_len == 2048 and args.batch == 50_000)
     traffic = SCAN_DRAM_BYTES_DEFAULT if default_run else None
     scan_mean_ms = statistics.mean(scan_ms)
-    achieved = cells_step / (scan_mean_ms * 1e-3) / 1e12
+    achieved = cells_timed / (sum(scan_ms) * 1e-3) / 1e12
+    src = (f"measured: pipe probe with one packed int16 DPX add-max and one packed f16 FMA-relu per step "
+           f"(both 16-lane pipes busy): {probe[2]:.3f} warp-instructions per SM clock x 32 cells x {sms} SMs "
+           f"x {clk_mhz:.0f} MHz" if measured else
+           f"nominal: {sms} SMs x 4 sub-partitions x 32 cells/clk x {clk_mhz:.0f} MHz")
     return {
         "metric": METRIC, "value": round(gcups, 3), "unit": "GCUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(t * 1e3 / args.steps, 3), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "int16", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f16" if lanes.startswith("f16") else "int16",
+        "data": "synthetic",
         "config": {**workload_config(wl, genome, lengths, frag_len, args, world),
                    "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
                    "scan_tune": tune, "autotune": tuned, "scan_lanes": lanes},
@@ -272,9 +307,8 @@ def bench_line(*, gcups, t, world, args, reads_s, e2e, launches, sms, probe, max
         "gpu_launches": int(launches),
         "roofline": {"bound": "alu", "kernel": "k_scan (phase-one scan + per-read fragment top-4)",
                      "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "Tcell/s",
-                     "frac": round(achieved / peak, 4), "traffic": traffic,
-                     "peak_source": f"derived: {sms} SMs x 4 sub-partitions x 32 cells/clk (16-lane integer/DPX "
-                                    "pipe + 16-lane FMA pipe, packed 16-bit x2, 2 ops per cell) x 2070 MHz",
+                     "frac": round(achieved / peak, 4), "traffic": traffic, "peak_source": src,
+                     "peak_nominal": round(nominal, 3), "frac_of_nominal": round(achieved / nominal, 4),
                      "scan_ms_per_step": round(scan_mean_ms, 3),
                      "peak_dpx_pipe_only": round(dpx_only, 3) if dpx_only else None,
                      "frac_of_dpx_pipe_only": round(achieved / dpx_only, 4) if dpx_only else None},
@@ -302,7 +336,8 @@ def main():
     R = int(lengths.shape[0])
     max_len = int(lengths.max())
     nm, nmm, go, ge, W = wl.nw
-    cells_step = cells_of(lengths, genome.shape[0], wl.frag_len, args.read_step)
+    parts = batches(seq, off, args.batch)
+    nb = len(parts)
 
     # CPU baseline first (rank 0, N = 1), before the GPU is busy
     cpu = None
@@ -323,14 +358,18 @@ def main():
     mss.mss_set_read_step(g, args.read_step)
     mss.mss_scan_timing(g, True)
     stream = torch.cuda.Stream(device=dev)
-    d_seq = torch.from_numpy(seq).to(dev)
-    d_off = torch.from_numpy(off).to(dev)
-    d_hits = torch.empty(R * 32, dtype=torch.uint8, device=dev)
-    d_alns = torch.empty(R * 24, dtype=torch.uint8, device=dev)
+    d_parts = [(torch.from_numpy(s).to(dev), torch.from_numpy(o).to(dev), int(o.shape[0] - 1)) for s, o in parts]
+    Rb = max(p[2] for p in d_parts)
+    d_hits = torch.empty(Rb * 32, dtype=torch.uint8, device=dev)
+    d_alns = torch.empty(Rb * 24, dtype=torch.uint8, device=dev)
     stride = 4 * max_len + 64
-    d_cig = torch.empty(R * stride, dtype=torch.uint8, device=dev)
+    d_cig = torch.empty(Rb * stride, dtype=torch.uint8, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
+    def part_cells(F):
+        return [cells_of(np.diff(o), genome.shape[0], F, args.read_step) for _, o in parts]
+
+    cells_b = part_cells(wl.frag_len)
     tuned = None
     if args.autotune:
         # an evenly spaced sample of the reads (all lengths), outside the timed region
@@ -342,16 +381,17 @@ def main():
         tuned["sample_reads"] = n
         tuned["seconds"] = round(time.perf_counter() - t0, 1)
         info = g.info()
-        cells_step = cells_of(lengths, genome.shape[0], info["frag_len"], args.read_step)
+        cells_b = part_cells(info["frag_len"])
 
-    def step():
-        mss.mss_map_reads_device(g, d_seq, d_off, R, max_len, wl.match, wl.mismatch, d_hits, stream=stream)
-        mss.nw_align_device(g, d_seq, d_off, R, max_len, d_hits, d_alns, d_cig, stride, nm, nmm, go, ge, W,
+    def step(b):
+        d_seq, d_off, Rk = d_parts[b]
+        mss.mss_map_reads_device(g, d_seq, d_off, Rk, max_len, wl.match, wl.mismatch, d_hits, stream=stream)
+        mss.nw_align_device(g, d_seq, d_off, Rk, max_len, d_hits, d_alns, d_cig, stride, nm, nmm, go, ge, W,
                             stream=stream)
 
     with torch.cuda.stream(stream):
         for i in range(args.warmup):
-            step()
+            step(i % nb)
         mss.mss_sync(g, stream=stream)
         probe = mss.mss_probe_pipes()[0] if rank == 0 else None   # pipe rates, outside the timed region
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -365,7 +405,7 @@ def main():
         for k in range(args.steps):
             flush.fill_(k & 0xFF)                    # evict the genome and workspaces from L2
             ev[k][0].record(stream)
-            step()
+            step(k % nb)
             ev[k][1].record(stream)
             scan_ms.append(mss.mss_scan_time_ms(g))  # waits for this step's scan
         torch.cuda.synchronize(dev)
@@ -381,43 +421,51 @@ def main():
         tt = torch.tensor([t_local], dtype=torch.float64, device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t = float(tt.item())
-    total_cells = cells_step * args.steps * world
-    gcups = total_cells / t / 1e9
-    reads_s = R * args.steps * world / t
+    cells_timed = sum(cells_b[k % nb] for k in range(args.steps))
+    reads_timed = sum(d_parts[k % nb][2] for k in range(args.steps))
+    gcups = cells_timed * world / t / 1e9
+    reads_s = reads_timed * world / t
 
     # end to end through the host-pointer call (pinned host buffers, copies inside the timing)
     e2e = None
     if not args.no_e2e:
-        h_seq = torch.from_numpy(seq).pin_memory()
-        h_off = torch.from_numpy(off).pin_memory()
-        h_hits = torch.empty(R * 32, dtype=torch.uint8).pin_memory()
-        h_alns = torch.empty(R * 24, dtype=torch.uint8).pin_memory()
-        h_cig = torch.empty(R * stride, dtype=torch.uint8).pin_memory()
-        mss.mss_map_align(g, h_seq, h_off, wl.match, wl.mismatch, wl.nw, h_hits, h_alns, h_cig, stride,
-                          stream=stream)
+        h_parts = [(torch.from_numpy(s).pin_memory(), torch.from_numpy(o).pin_memory()) for s, o in parts]
+        h_hits = torch.empty(Rb * 32, dtype=torch.uint8).pin_memory()
+        h_alns = torch.empty(Rb * 24, dtype=torch.uint8).pin_memory()
+        h_cig = torch.empty(Rb * stride, dtype=torch.uint8).pin_memory()
+
+        def e2e_step(b):
+            h_seq, h_off = h_parts[b]
+            Rk = int(h_off.shape[0] - 1)
+            mss.mss_map_align(g, h_seq, h_off, wl.match, wl.mismatch, wl.nw, h_hits[:Rk * 32], h_alns[:Rk * 24],
+                              h_cig[:Rk * stride], stride, stream=stream)
+
+        e2e_step(0)
         if world > 1:
             dist.barrier()
         e2e_steps = max(1, args.steps)
         t0 = time.perf_counter()
-        for _ in range(e2e_steps):
-            mss.mss_map_align(g, h_seq, h_off, wl.match, wl.mismatch, wl.nw, h_hits, h_alns, h_cig, stride,
-                              stream=stream)
+        for k in range(e2e_steps):
+            e2e_step(k % nb)
         te = time.perf_counter() - t0
         if world > 1:
             tt = torch.tensor([te], dtype=torch.float64, device=dev)
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
             te = float(tt.item())
-        e2e = {"value": round(cells_step * e2e_steps * world / te / 1e9, 3), "unit": "GCUPS",
-               "h2d_bytes_per_step": int(seq.nbytes + off.nbytes),
-               "d2h_bytes_per_step": int(R * 32 + R * 24 + R * stride),
-               "reads_per_s": round(R * e2e_steps * world / te, 1)}
+        e_cells = sum(cells_b[k % nb] for k in range(e2e_steps))
+        e_reads = sum(int(parts[k % nb][1].shape[0] - 1) for k in range(e2e_steps))
+        h2d = sum(int(parts[k % nb][0].nbytes + parts[k % nb][1].nbytes) for k in range(e2e_steps)) // e2e_steps
+        d2h = sum(int(parts[k % nb][1].shape[0] - 1) * (32 + 24 + stride) for k in range(e2e_steps)) // e2e_steps
+        e2e = {"value": round(e_cells * world / te / 1e9, 3), "unit": "GCUPS",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "reads_per_s": round(e_reads * world / te, 1)}
 
     if rank == 0:
         line = bench_line(
             gcups=gcups, t=t, world=world, args=args, reads_s=reads_s, e2e=e2e, launches=launches,
             sms=props.multi_processor_count, probe=probe, max_len=max_len, wl=wl, genome=genome,
             lengths=lengths, frag_len=info["frag_len"], tune=mss.mss_get_tune(g), tuned=tuned,
-            cells_step=cells_step, scan_ms=scan_ms, cpu=cpu, clk=clk)
+            cells_timed=cells_timed, scan_ms=scan_ms, cpu=cpu, clk=clk)
         print(json.dumps(line), flush=True)
     g.close()
     if world > 1:

@@ -49,7 +49,7 @@ def _lib():
             lib.gen_reads.argtypes = [ctypes.c_uint64, P, ctypes.c_int64, ctypes.c_int32, P, ctypes.c_double,
                                       ctypes.c_double, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                       ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_int32,
-                                      P, P, P, P, P, P]
+                                      P, P, P, P, P, P, P]
             lib.gen_reads.restype = ctypes.c_int
             lib.gen_lengths.argtypes = [ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32, P, ctypes.c_int32,
                                         ctypes.c_double, ctypes.c_double, ctypes.c_int32, ctypes.c_int32, P]
@@ -112,6 +112,9 @@ class Reads:
     true_strand: np.ndarray  # int8 [R]
     n_sub: np.ndarray        # int32 [R]
     n_gap: np.ndarray        # int32 [R]
+    true_rel: np.ndarray | None = None  # int32 per base (same offsets as seq): genome position of
+    #                                     SEQ base j (forward-strand orientation) minus true_start,
+    #                                     -1 for an inserted base; only when asked for
 
     @property
     def count(self) -> int:
@@ -131,7 +134,14 @@ class Reads:
         np.cumsum(lens, out=offs[1:])
         seq = np.concatenate([self.seq[self.offsets[i]:self.offsets[i + 1]] for i in idx]) if idx.size else \
             np.zeros(0, np.uint8)
-        return Reads(seq, offs, self.true_start[idx], self.true_strand[idx], self.n_sub[idx], self.n_gap[idx])
+        rel = np.concatenate([self.true_rel[self.offsets[i]:self.offsets[i + 1]] for i in idx]) \
+            if self.true_rel is not None and idx.size else None
+        return Reads(seq, offs, self.true_start[idx], self.true_strand[idx], self.n_sub[idx], self.n_gap[idx], rel)
+
+    def true_positions(self, i: int) -> np.ndarray:
+        """Genome position of every SEQ base of read i (-1 for inserted bases)."""
+        rel = self.true_rel[self.offsets[i]:self.offsets[i + 1]].astype(np.int64)
+        return np.where(rel >= 0, rel + int(self.true_start[i]), -1)
 
 
 def make_lengths(spec: ReadSpec, seed: int) -> np.ndarray:
@@ -147,7 +157,7 @@ def make_lengths(spec: ReadSpec, seed: int) -> np.ndarray:
     return out
 
 
-def make_reads(genome: np.ndarray, spec: ReadSpec, seed: int) -> Reads:
+def make_reads(genome: np.ndarray, spec: ReadSpec, seed: int, positions: bool = False) -> Reads:
     lengths = make_lengths(spec, seed)
     R = spec.count
     parts = []
@@ -166,22 +176,15 @@ def make_reads(genome: np.ndarray, spec: ReadSpec, seed: int) -> Reads:
         st = np.empty(n, dtype=np.int8)
         ns = np.empty(n, dtype=np.int32)
         ng = np.empty(n, dtype=np.int32)
+        rel = np.empty(int(offs[-1]), dtype=np.int32) if positions else None
         rc = _lib().gen_reads(seed + 7919 * li, _ptr(genome), genome.shape[0], n, _ptr(lens), float(lo), float(hi),
                               spec.gap_mode, spec.gap_count_max, spec.gap_min, spec.gap_max, spec.gap_p,
                               spec.deam_rate, spec.deam_len, _ptr(seq), _ptr(offs), _ptr(ts), _ptr(st),
-                              _ptr(ns), _ptr(ng))
+                              _ptr(ns), _ptr(ng), _ptr(rel) if positions else None)
         if rc != 0:
             raise RuntimeError(f"gen_reads failed ({rc})")
-        parts.append(Reads(seq, offs, ts, st, ns, ng))
-    if len(parts) == 1:
-        return parts[0]
-    seq = np.concatenate([p.seq for p in parts])
-    lens = np.concatenate([p.lengths for p in parts]).astype(np.int64)
-    offs = np.zeros(R + 1, dtype=np.int64)
-    np.cumsum(lens, out=offs[1:])
-    return Reads(seq, offs, np.concatenate([p.true_start for p in parts]),
-                 np.concatenate([p.true_strand for p in parts]), np.concatenate([p.n_sub for p in parts]),
-                 np.concatenate([p.n_gap for p in parts]))
+        parts.append(Reads(seq, offs, ts, st, ns, ng, rel))
+    return _concat(parts)
 
 
 @dataclass
@@ -250,17 +253,35 @@ def scaled(wl: Workload, genome_len: int | None = None, reads: int | None = None
                     wl.match, wl.mismatch, wl.nw, wl.seed, wl.notes)
 
 
-def materialize(wl: Workload):
-    """Genome (uint8 ASCII) and Reads for a workload."""
-    genome = make_genome(wl.genome, wl.seed)
-    parts = [make_reads(genome, rs, wl.seed * 31 + i) for i, rs in enumerate(wl.reads)]
+def _concat(parts: list) -> Reads:
     if len(parts) == 1:
-        return genome, parts[0]
+        return parts[0]
     R = sum(p.count for p in parts)
     seq = np.concatenate([p.seq for p in parts])
     lens = np.concatenate([p.lengths for p in parts]).astype(np.int64)
     offs = np.zeros(R + 1, dtype=np.int64)
     np.cumsum(lens, out=offs[1:])
-    return genome, Reads(seq, offs, np.concatenate([p.true_start for p in parts]),
-                         np.concatenate([p.true_strand for p in parts]), np.concatenate([p.n_sub for p in parts]),
-                         np.concatenate([p.n_gap for p in parts]))
+    rel = np.concatenate([p.true_rel for p in parts]) if all(p.true_rel is not None for p in parts) else None
+    return Reads(seq, offs, np.concatenate([p.true_start for p in parts]),
+                 np.concatenate([p.true_strand for p in parts]), np.concatenate([p.n_sub for p in parts]),
+                 np.concatenate([p.n_gap for p in parts]), rel)
+
+
+def read_set(wl: Workload, genome: np.ndarray, rank: int = 0, positions: bool = False) -> Reads:
+    """All reads of a workload in order (its ReadSpecs one after another), drawn for one rank:
+    rank 0 gives the reads of ``materialize``; other ranks get other seeds.  positions: also
+    record every base's true genome position (``Reads.true_rel``)."""
+    return _concat([make_reads(genome, rs, wl.seed * 31 + i + 1000003 * rank, positions)
+                    for i, rs in enumerate(wl.reads)])
+
+
+def batch_index(R: int, n_batches: int, b: int) -> np.ndarray:
+    """Reads of batch b when R reads are dealt into n_batches batches: b, b + n, b + 2n, ...
+    (every batch gets the same mix of read lengths and divergences)."""
+    return np.arange(b, R, n_batches, dtype=np.int64)
+
+
+def materialize(wl: Workload):
+    """Genome (uint8 ASCII) and Reads for a workload."""
+    genome = make_genome(wl.genome, wl.seed)
+    return genome, read_set(wl, genome, 0)

@@ -175,7 +175,7 @@ int gen_genome(uint64_t seed, int64_t G, double gc, double copy_frac, int64_t co
 int gen_reads(uint64_t seed, const char* genome, int64_t G, int32_t R, const int32_t* lengths, double sub_lo,
               double sub_hi, int32_t gap_mode, int32_t gap_count_max, int32_t gap_min, int32_t gap_max, double gap_p,
               double deam_rate, int32_t deam_len, char* reads, int64_t* offsets, int64_t* true_start,
-              int8_t* true_strand, int32_t* n_sub, int32_t* n_gap) {
+              int8_t* true_strand, int32_t* n_sub, int32_t* n_gap, int32_t* true_rel) {
   rng_t r;
   rng_seed(&r, seed ^ 0x5EEDF00Dull);
   /* prefix count of N for span checks */
@@ -186,7 +186,8 @@ int gen_reads(uint64_t seed, const char* genome, int64_t G, int32_t R, const int
   int32_t maxlen = 0;
   for (int32_t i = 0; i < R; ++i) maxlen = lengths[i] > maxlen ? lengths[i] : maxlen;
   char* buf = (char*)malloc((size_t)maxlen + 8);
-  if (!buf) { free(ncount); return -2; }
+  int32_t* rel = (int32_t*)malloc(sizeof(int32_t) * ((size_t)maxlen + 8));
+  if (!buf || !rel) { free(buf); free(rel); free(ncount); return -2; }
   offsets[0] = 0;
   for (int32_t i = 0; i < R; ++i) {
     int32_t m = lengths[i];
@@ -222,13 +223,13 @@ int gen_reads(uint64_t seed, const char* genome, int64_t G, int32_t R, const int
         t = glen[b]; glen[b] = glen[b - 1]; glen[b - 1] = t;
       }
     int64_t span = (int64_t)m + del_total; /* upper bound on genome bases consumed */
-    if (span > G) { free(buf); free(ncount); return -3; }
+    if (span > G) { free(buf); free(rel); free(ncount); return -3; }
     int64_t start = -1;
     for (int attempt = 0; attempt < 100000; ++attempt) {
       int64_t s = (int64_t)rng_below(&r, (uint64_t)(G - span + 1));
       if (ncount[s + span] - ncount[s] == 0) { start = s; break; }
     }
-    if (start < 0) { free(buf); free(ncount); return -4; }
+    if (start < 0) { free(buf); free(rel); free(ncount); return -4; }
     double p = sub_lo + (sub_hi - sub_lo) * rng_unit(&r);
     uint32_t sub_thr = prob_to_thr(p);
     int32_t k = 0, ev = 0, subs = 0, gapb = 0;
@@ -240,6 +241,7 @@ int gen_reads(uint64_t seed, const char* genome, int64_t G, int32_t R, const int
           gapb += glen[ev];
         } else {
           for (int32_t t = 0; t < glen[ev] && k < m; ++t) {
+            rel[k] = -1;                       /* an inserted base has no genome position */
             buf[k++] = BASES[rng_below(&r, 4)];
             ++gapb;
           }
@@ -247,6 +249,7 @@ int gen_reads(uint64_t seed, const char* genome, int64_t G, int32_t R, const int
         ++ev;
       }
       if (k >= m) break;
+      rel[k] = (int32_t)(gp - start);
       char b = genome[gp++];
       if (b >= 'a' && b <= 'z') b = (char)(b - 32);
       if (rng_bern32(&r, sub_thr)) { b = rng_other_base(&r, b); ++subs; }
@@ -259,6 +262,9 @@ int gen_reads(uint64_t seed, const char* genome, int64_t G, int32_t R, const int
     } else {
       memcpy(dst, buf, (size_t)m);
     }
+    /* true position of each base in the forward-strand orientation of the read (SAM's SEQ),
+       relative to true_start; -1 for inserted bases */
+    if (true_rel) memcpy(true_rel + offsets[i], rel, sizeof(int32_t) * (size_t)m);
     if (deam_rate > 0 && deam_len > 0) {
       for (int32_t t = 0; t < deam_len && t < m; ++t) {
         double pr = deam_rate * (double)(deam_len - t) / (double)deam_len;
@@ -272,6 +278,7 @@ int gen_reads(uint64_t seed, const char* genome, int64_t G, int32_t R, const int
     if (n_gap) n_gap[i] = gapb;
   }
   free(buf);
+  free(rel);
   free(ncount);
   return 0;
 }

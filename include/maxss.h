@@ -245,6 +245,18 @@ MSS_API mss_status mss_genome_codes(const mss_ctx* ctx, int64_t start, int64_t n
  */
 MSS_API mss_status mss_probe_pipes(double* rates3, double* clk_mhz);
 
+/*
+ * Self-check of failure detection (a property of this library, not of the paper's method):
+ * every device wait of the kernels here is bounded and, when it gives up, sets an error bit
+ * that the next synchronising call returns as MSS_ETIMEOUT instead of hanging.  This call
+ * launches one block that waits limit_us microseconds (1 .. 1,000,000) on an mbarrier phase
+ * that nothing completes, with the same bounded wait the scan uses, then synchronises the
+ * stream.  Returns MSS_ETIMEOUT when the wait gave up as designed (the error word is cleared
+ * and the context stays usable), MSS_EINVAL for a null context or a limit out of range,
+ * MSS_ECUDA on a launch failure.
+ */
+MSS_API mss_status mss_check_wait_timeout(mss_ctx* ctx, uint32_t limit_us, void* stream);
+
 /* ==========================================================================================
  * Learned fragment proposal (a step added to the method; the paper has none).  A small 1-D
  * CNN (one-hot bases -> 4 x conv1d(128 channels, kernel 7, "same", ReLU) -> max over

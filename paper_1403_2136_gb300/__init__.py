@@ -32,7 +32,7 @@ EXPORTS = ("mss_load_genome", "mss_load_genome_device", "mss_get_info", "mss_set
            "mss_set_second_rule",
            "mss_get_read_step", "mss_set_tune",
            "mss_get_tune", "mss_map_reads", "mss_map_reads_device", "nw_align", "nw_align_device", "nw_align_device_noalloc", "mss_map_align", "mss_sync",
-           "mss_autotune", "mss_scan_timing", "mss_scan_time_ms", "mss_launch_count", "mss_genome_codes", "mss_probe_pipes", "mss_prop_create", "mss_prop_free", "mss_prop_param_count",
+           "mss_autotune", "mss_scan_timing", "mss_scan_time_ms", "mss_launch_count", "mss_genome_codes", "mss_probe_pipes", "mss_check_wait_timeout", "mss_prop_create", "mss_prop_free", "mss_prop_param_count",
            "mss_prop_get_params", "mss_prop_set_params", "mss_prop_read_codes", "mss_prop_window_codes",
            "mss_prop_embed_device", "mss_prop_grad_device", "mss_prop_train_step", "mss_prop_build_index",
            "mss_map_reads_proposed", "mss_prop_save", "mss_prop_load", "mss_prop_launch_count", "mss_free",
@@ -110,6 +110,7 @@ def load_library(path: str = LIB_PATH):
         "mss_launch_count": ([P], i64),
         "mss_genome_codes": ([P, i64, i64, P], i32),
         "mss_probe_pipes": ([ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], i32),
+        "mss_check_wait_timeout": ([P, ctypes.c_uint32, P], i32),
         "mss_prop_create": ([ctypes.POINTER(P), ctypes.c_uint64, P], i32),
         "mss_prop_free": ([P], None),
         "mss_prop_param_count": ([], i64),
@@ -404,6 +405,12 @@ def mss_probe_pipes():
     clk = ctypes.c_double()
     _check(load_library().mss_probe_pipes(r, ctypes.byref(clk)), "mss_probe_pipes")
     return list(r), clk.value
+
+
+def mss_check_wait_timeout(g: Genome, limit_us: int = 2000, stream=None) -> int:
+    """Run the bounded-wait self-check; returns its status (MSS_ETIMEOUT when the wait gave up
+    as designed) without raising, so that the caller can check the code."""
+    return int(load_library().mss_check_wait_timeout(g.handle, limit_us, _stream_ptr(stream)))
 
 
 def hits_from_bytes(buf) -> np.ndarray:

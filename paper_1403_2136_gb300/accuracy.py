@@ -1,17 +1,13 @@
-"""Truth-based mapping accuracy of phase two's alignments ("Mapping qualities, read lengths,
-SAM output": a read counts as correctly mapped when at least one of its bases is aligned to
-its true position).
+"""Truth-based mapping accuracy of phase two's alignments (the paper's "Measure of accuracy
+and error": a read counts as aligned correctly when at least one of its bases is aligned to the
+same genome base as in its true alignment).
 
 Host code on the outputs of the path: the hits (strand, repeat flag, scores) and alignments
-(genome start, CIGAR) of `mss_map_align` / `nw_align`, against the truth that the synthetic
-read generator records (source start and strand).  The SEQ orientation of an alignment is the
-forward genome strand, and the generator builds every read from its source window in that
-orientation with indels only after the first base, so SEQ base j before the read's first indel
-lies at `true_start + j` on either strand.  A read is correct when its strand is the true one
-and some aligned base j (CIGAR M) sits at `true_start + j`.  Past an indel this position is
-not the base's true one; a base there can only match it on an alignment that is shifted by
-exactly that indel, which the check then counts as correct (rare, and it leaves the error-free
-prefix unaligned).
+(genome start, CIGAR) of `mss_map_align` / `nw_align`, against the true alignment that the
+synthetic read generator records for every base: the genome position each base of the read
+was copied from (in SAM's SEQ orientation, the forward genome strand, on either strand), or
+none for a base inserted by an indel.  A read is correct when it is mapped, on its true
+strand, and some aligned base j (CIGAR M) sits at base j's true position.
 
     python -m paper_1403_2136_gb300.accuracy --workload bact-4.6M --reads 30000
 
@@ -58,16 +54,17 @@ def mapped_mask(hits, alns) -> np.ndarray:
     return ((hits["flags"] & 1) == 0) & (alns["score"] != none) & (alns["cigar_len"] > 0)
 
 
-def correct_mask(hits, alns, cigars, lengths, true_start, true_strand) -> np.ndarray:
-    """Per read: mapped, on the true strand, with some aligned base at its true position."""
+def correct_mask(hits, alns, cigars, true_positions, true_strand) -> np.ndarray:
+    """Per read: mapped, on the true strand, with some aligned base at its true position.
+    true_positions[i]: the true genome position of every SEQ base of read i (-1: inserted)."""
     mapped = mapped_mask(hits, alns)
-    out = np.zeros(len(lengths), dtype=bool)
+    out = np.zeros(len(true_positions), dtype=bool)
     for i in np.nonzero(mapped)[0]:
         if int(hits["strand"][i]) != int(true_strand[i]):
             continue
-        m = int(lengths[i])
-        pos = base_positions(int(alns["gstart"][i]), cigars[i], m)
-        out[i] = bool(np.any(pos == int(true_start[i]) + np.arange(m)))
+        truth = np.asarray(true_positions[i], dtype=np.int64)
+        pos = base_positions(int(alns["gstart"][i]), cigars[i], truth.shape[0])
+        out[i] = bool(np.any((pos >= 0) & (pos == truth)))
     return out
 
 
@@ -78,12 +75,12 @@ def mapq_of(hits) -> np.ndarray:
                     dtype=np.int32)
 
 
-def report(hits, alns, cigars, lengths, true_start, true_strand, groups: dict, mapq=None,
+def report(hits, alns, cigars, true_positions, true_strand, groups: dict, mapq=None,
            thresholds=(0, 20, 30)) -> dict:
     """Mapped and correct fractions per read group (name -> index array), overall and at MAPQ
     thresholds (a read counts at threshold t when it is mapped with MAPQ >= t)."""
     mapped = mapped_mask(hits, alns)
-    correct = correct_mask(hits, alns, cigars, lengths, true_start, true_strand)
+    correct = correct_mask(hits, alns, cigars, true_positions, true_strand)
     mq = mapq if mapq is not None else mapq_of(hits)
     out = {}
     for name, idx in groups.items():
@@ -112,9 +109,10 @@ def main(argv=None) -> int:
 
     wl = gen.scaled(gen.workloads()[args.workload], genome_len=args.genome or None, reads=args.reads)
     genome = gen.make_genome(wl.genome, wl.seed)
-    parts = [(gen.make_reads(genome, rs, wl.seed * 31 + i), rs) for i, rs in enumerate(wl.reads)]
+    parts = [(gen.make_reads(genome, rs, wl.seed * 31 + i, positions=True), rs) for i, rs in enumerate(wl.reads)]
     g = mss.mss_load_genome(genome, frag_len=wl.frag_len, max_read_len=max(int(p.lengths.max()) for p, _ in parts))
-    out = {"workload": wl.name, "criterion": "strand right and some aligned base at its true position",
+    out = {"workload": wl.name, "criterion": "strand right and some aligned base at its true position "
+                                             "(the true alignment of every base)",
            "groups": {}}
     for k, (reads, spec) in enumerate(parts):
         hits, alns, cig = mss.mss_map_align(g, reads.seq, reads.offsets, wl.match, wl.mismatch, wl.nw)
@@ -128,7 +126,8 @@ def main(argv=None) -> int:
             name = (f"{lens[0]}-{lens[-1]} bp" if len(lens) > 3 else "/".join(map(str, lens)) + " bp") + \
                 (f", subs {lo:.0%}" if lo == hi else f", subs {lo:.0%}-{hi:.0%}")
             groups[name] = np.arange(bounds[li], bounds[li + 1])
-        out["groups"].update(report(hits, alns, cigars, reads.lengths, reads.true_start, reads.true_strand, groups))
+        truth = [reads.true_positions(i) for i in range(R)]
+        out["groups"].update(report(hits, alns, cigars, truth, reads.true_strand, groups))
     g.close()
     print(json.dumps(out, indent=1))
     return 0

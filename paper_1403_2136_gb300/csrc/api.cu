@@ -851,6 +851,15 @@ mss_status mss_probe_pipes(double* rates3, double* clk_mhz) {
   return MSS_OK;
 }
 
+mss_status mss_check_wait_timeout(mss_ctx* c, uint32_t limit_us, void* stream) {
+  if (check_ctx(c)) return MSS_EINVAL;
+  if (limit_us < 1 || limit_us > 1000000) return fail(MSS_EINVAL, "wait limit must be 1 us .. 1 s");
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(launch_wait_selfcheck(c->d_err, (uint64_t)limit_us * 1000ull, s), "wait self-check kernel");
+  c->launches += 1;
+  return read_err(c, s);
+}
+
 void mss_free(mss_ctx* c) {
   if (!c) return;
   if (c->graph) cudaGraphExecDestroy(c->graph);

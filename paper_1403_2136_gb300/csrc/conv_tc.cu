@@ -75,7 +75,8 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
   return d;
 }
 
-// 2-D tiled TMA load of box (x .. x + 7 channels, y .. y + 133 rows) completing on bar
+// 2-D tiled TMA load of one 64-channel half of an item's input tile (channels x .. x + 63,
+// rows y .. y + 133, 128-byte rows in the 128-byte swizzle) completing on bar
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int32_t x, int32_t y,
                                             uint64_t* bar) {
   asm volatile(

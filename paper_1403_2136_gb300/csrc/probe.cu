@@ -83,4 +83,20 @@ cudaError_t probe_pipes(double* rates3, double* clk_mhz) {
   return e;
 }
 
+// Self-check of the bounded-wait error path: one thread waits, with the given limit, on an
+// mbarrier phase that nothing completes (no copy armed, no arrival), then reports the time-out
+// through the context's error word exactly as the scan does, and returns.
+__global__ void k_wait_selfcheck(int32_t* err, uint64_t limit_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  if (!mbar_wait(&bar, 0u, limit_ns)) atomicOr(err, ERR_TIMEOUT);
+}
+
+cudaError_t launch_wait_selfcheck(int32_t* err, uint64_t limit_ns, cudaStream_t s) {
+  k_wait_selfcheck<<<1, 32, 0, s>>>(err, limit_ns);
+  return cudaGetLastError();
+}
+
 }  // namespace mss

@@ -5,10 +5,12 @@
 // Network: one-hot bases (N = all zero) -> 4 x [conv1d k=7 "same", 128 channels, bias, ReLU]
 // -> max over positions -> L2 normalisation.  Weights BF16, accumulation FP32.
 //
-// Kernels (all here, the 128->128 contractions on tensor cores through mma.sync BF16):
+// Kernels here (the 128 -> 128 conv itself, forward and backward-data, runs on the
+// fifth-generation tensor cores in conv_tc.cu; the read x fragment score GEMM with its fused
+// top K in score_tc.cu):
 //   k_embed_l1      first layer (4 -> 128) as a gather-sum of per-base weight rows
-//   (the 128 -> 128 conv, forward and backward-data, runs on the tensor cores: conv_tc.cu)
-//   k_conv_wgrad    weight gradient, a GEMM over positions per tap (fp32 atomics across CTAs)
+//   k_conv_wgrad    weight gradient, a GEMM over positions per tap on the BF16 mma.sync path
+//                   (fp32 atomics across CTAs)
 //   k_pool_norm     max over positions (first argmax kept), L2 norm
 //   k_pool_norm_bwd gradient of the norm routed to the argmax positions
 //   k_l1_wgrad      first-layer weight/bias gradients; k_bias_grad: bias gradients

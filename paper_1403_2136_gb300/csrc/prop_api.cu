@@ -16,9 +16,13 @@ using namespace mss;
 
 namespace {
 
-struct Buf {
+struct Buf {  // a device buffer owned by its holder: freed by release() or when it goes out of scope
   void* p = nullptr;
   size_t cap = 0;
+  Buf() = default;
+  Buf(const Buf&) = delete;
+  Buf& operator=(const Buf&) = delete;
+  ~Buf() { release(); }
   cudaError_t ensure(size_t bytes) {
     if (bytes <= cap) return cudaSuccess;
     if (p) cudaFree(p);
@@ -474,7 +478,8 @@ mss_status mss_map_reads_proposed(mss_ctx* ctx, mss_prop* p, const char* d_reads
   if (d_top_score) {
     std::vector<float> t1(R);
     for (int32_t i = 0; i < R; ++i) t1[i] = top[(size_t)i * K];
-    PCK(cudaMemcpy(d_top_score, t1.data(), (size_t)R * 4, cudaMemcpyHostToDevice), "top score");
+    PCK(cudaMemcpyAsync(d_top_score, t1.data(), (size_t)R * 4, cudaMemcpyHostToDevice, s), "top score");
+    PCK(cudaStreamSynchronize(s), "top score");   // t1 lives on this stack frame
   }
   std::vector<int32_t> fb;
   for (int32_t i = 0; i < R; ++i)
@@ -483,7 +488,8 @@ mss_status mss_map_reads_proposed(mss_ctx* ctx, mss_prop* p, const char* d_reads
   if (fb.empty()) return MSS_OK;
   // gather the fallback reads into a compact batch, map them exhaustively, scatter the hits
   std::vector<int64_t> hoff(R + 1);
-  PCK(cudaMemcpy(hoff.data(), d_offsets, (size_t)(R + 1) * 8, cudaMemcpyDeviceToHost), "offsets read");
+  PCK(cudaMemcpyAsync(hoff.data(), d_offsets, (size_t)(R + 1) * 8, cudaMemcpyDeviceToHost, s), "offsets read");
+  PCK(cudaStreamSynchronize(s), "offsets read");
   std::vector<int64_t> noff(fb.size() + 1, 0);
   for (size_t j = 0; j < fb.size(); ++j) noff[j + 1] = noff[j] + (hoff[fb[j] + 1] - hoff[fb[j]]);
   const int32_t nfb = (int32_t)fb.size();

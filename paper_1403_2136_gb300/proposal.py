@@ -39,26 +39,55 @@ def exhaustive_labels(torch, g, d_seq, d_off, R, max_len, match, mismatch, strea
     return hits_from_bytes(d_hits.cpu()).copy()
 
 
+def mine_hard(torch, prop: Proposal, g, d_seq, d_off, R, max_len, match, mismatch, K, stream=None):
+    """The model's own top K fragments of every training read over the whole fragment index
+    (index rebuilt with the current weights): the hard negatives of the next steps."""
+    prop.build_index(g, max_len, stream=stream)
+    d_out = torch.empty(R * 32, dtype=torch.uint8, device="cuda")
+    d_cand = torch.empty(R * K, dtype=torch.int32, device="cuda")
+    prop.map_reads(g, d_seq, d_off, R, max_len, match, mismatch, K, -1e30, d_out, d_cand=d_cand, stream=stream)
+    torch.cuda.synchronize()
+    return d_cand.cpu().numpy().reshape(R, K)
+
+
 def train(torch, prop: Proposal, g, d_seq, d_off, lens, labels, F: int, max_len: int, steps: int, batch: int,
-          lr: float, temperature: float, seed: int = 1, log_every: int = 50, log=None):
-    """Contrastive training on exhaustive-scan labels.  Returns the list of step losses."""
+          lr: float, temperature: float, seed: int = 1, log_every: int = 50, log=None, mine_every: int = 0,
+          hard: int = 0, match: int = 5, mismatch: int = -4, K: int = 64):
+    """Contrastive training on exhaustive-scan labels.  The candidates of a step are the best
+    and second-best fragments of its reads and, with mining on, each read's `hard` highest-
+    ranked wrong fragments from the model's own top K over the whole index (refreshed every
+    `mine_every` steps).  Returns the list of step losses."""
     rng = np.random.default_rng(seed)
     ok = np.nonzero((labels["best_score"] > 0) & ((labels["flags"] & 1) == 0))[0]  # confidently mapped reads
     win = F + max_len - 1
     B = min(batch, ok.size)
+    cmax = min(1024, B * (2 + hard))
     d_rcodes = torch.empty(B * max_len, dtype=torch.uint8, device="cuda")
     d_rlens = torch.empty(B, dtype=torch.int32, device="cuda")
-    d_ccodes = torch.empty(2 * B * win, dtype=torch.uint8, device="cuda")
-    d_clens = torch.empty(2 * B, dtype=torch.int32, device="cuda")
+    d_ccodes = torch.empty(cmax * win, dtype=torch.uint8, device="cuda")
+    d_clens = torch.empty(cmax, dtype=torch.int32, device="cuda")
     losses = []
+    mined = None
+    R = lens.shape[0]
     for step in range(steps):
+        if hard > 0 and mine_every > 0 and step % mine_every == 0 and step > 0:
+            mined = mine_hard(torch, prop, g, d_seq, d_off, R, max_len, match, mismatch, K)
         pick = rng.choice(ok, size=B, replace=False)
         strand = labels["strand"][pick].astype(np.int8)
         prop.read_codes(d_seq, d_off, _dev(torch, pick.astype(np.int32)), _dev(torch, strand), B, max_len, d_rcodes,
                         d_rlens)
         b1 = labels["best_frag"][pick]
         b2 = labels["second_frag"][pick]
-        cand = np.unique(np.concatenate([b1, b2[b2 >= 0]]))
+        parts = [b1, b2[b2 >= 0]]
+        if mined is not None:
+            m = mined[pick]
+            wrong = m != b1[:, None]
+            # the first `hard` wrong fragments of each read's ranked list
+            rank = np.cumsum(wrong, axis=1)
+            parts.append(m[wrong & (rank <= hard) & (m >= 0)])
+        positives = np.unique(b1)
+        negatives = np.setdiff1d(np.concatenate(parts[1:]), positives)[:cmax - positives.size]
+        cand = np.concatenate([positives, negatives])
         pos = {int(f): i for i, f in enumerate(cand)}
         lab = np.array([pos[int(f)] for f in b1], dtype=np.int32)
         C = cand.size
@@ -98,78 +127,120 @@ def evaluate(torch, prop: Proposal, g, d_seq, d_off, R, max_len, match, mismatch
     return out
 
 
+def _genome_for(gen, spec: str):
+    """'name' or 'name@length' (the workload's genome recipe, scaled to length)."""
+    name, _, ln = spec.partition("@")
+    wl = gen.workloads()[name]
+    if ln:
+        wl = gen.scaled(wl, genome_len=int(ln))
+    return wl, gen.make_genome(wl.genome, wl.seed)
+
+
+def pick_tau(rows, target: float = 0.995):
+    """The smallest threshold whose top-1 agreement reaches the target (rows of evaluate());
+    the largest threshold when none does."""
+    ok = [r for r in rows if r["top1_agreement"] >= target]
+    return min(ok, key=lambda r: r["tau"])["tau"] if ok else max(r["tau"] for r in rows)
+
+
 def main(argv=None):
     import torch
 
     import gen
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="chrom-230M", choices=["chrom-230M", "ancient-2.4G"],
-                    help="genome and read shape (the genome is scaled to --genome-len)")
-    ap.add_argument("--genome-len", type=int, default=23_000_000, help="genome length (0: the workload's own)")
+    ap.add_argument("--train-genome", default="bact-4.6M", help="genome of the training labels: name[@length]")
+    ap.add_argument("--read-shape", default="chrom-230M", help="workload whose read recipe draws the reads")
     ap.add_argument("--train-reads", type=int, default=60_000)
-    ap.add_argument("--eval-reads", type=int, default=20_000)
     ap.add_argument("--steps", type=int, default=800)
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--temperature", type=float, default=0.05)
+    ap.add_argument("--mine-every", type=int, default=0, help="refresh the hard negatives every N steps (0: off)")
+    ap.add_argument("--hard", type=int, default=2, help="hard negatives per read from the model's own top K")
     ap.add_argument("--K", type=int, default=64)
-    ap.add_argument("--taus", type=str, default="-1e30,0.5,0.7,0.8,0.9", help="comma-separated; pass as --taus=...")
-    ap.add_argument("--checkpoint", type=str, default="")
+    ap.add_argument("--evals", default="chrom-230M@23000000",
+                    help="comma-separated evaluation genomes name[@length] (held-out reads of the read shape)")
+    ap.add_argument("--eval-reads", type=int, default=20_000, help="held-out reads per genome (half choose tau)")
+    ap.add_argument("--taus", type=str, default="-1e30,0.3,0.4,0.5,0.6,0.7,0.8,0.9",
+                    help="comma-separated; pass as --taus=...")
+    ap.add_argument("--checkpoint", type=str, default="", help="save the trained weights here")
+    ap.add_argument("--load", type=str, default="", help="start from these weights")
     args = ap.parse_args(argv)
     log = lambda m: print(m, file=sys.stderr, flush=True)  # noqa: E731
 
-    wl = gen.workloads()[args.workload]
-    if args.genome_len:
-        wl = gen.scaled(wl, genome_len=args.genome_len)
-    t0 = time.perf_counter()
-    genome = gen.make_genome(wl.genome, wl.seed)
-    log(f"genome of {genome.shape[0]} bases in {time.perf_counter() - t0:.1f} s")
     F = 2048
-    spec = wl.reads[0]
-    max_len = 250 if spec.lognormal is None else int(spec.lognormal[3])
-    tr = gen.make_reads(genome, dataclasses.replace(spec, count=max(args.train_reads, 1)), wl.seed * 7 + 1)
-    ev = gen.make_reads(genome, dataclasses.replace(spec, count=args.eval_reads), wl.seed * 7 + 2)
+    rspec = gen.workloads()[args.read_shape].reads[0]
+    max_len = 250 if rspec.lognormal is None else int(rspec.lognormal[3])
+    wl, genome = _genome_for(gen, args.train_genome)
+    tr = gen.make_reads(genome, dataclasses.replace(rspec, count=max(args.train_reads, 1)), wl.seed * 7 + 1)
     g = mss_load_genome(genome, frag_len=F, max_read_len=max_len)
-    NF = g.info()["num_frags"]
     d_tseq, d_toff = _dev(torch, tr.seq), _dev(torch, tr.offsets)
     t0 = time.perf_counter()
     labels = exhaustive_labels(torch, g, d_tseq, d_toff, tr.count, max_len, wl.match, wl.mismatch)
     label_s = time.perf_counter() - t0
-    log(f"labels for {tr.count} reads in {label_s:.1f} s")
+    log(f"labels for {tr.count} reads on {genome.shape[0]} bp in {label_s:.1f} s")
     prop = Proposal(seed=1)
+    if args.load:
+        prop.load(args.load)
     t0 = time.perf_counter()
     losses = train(torch, prop, g, d_tseq, d_toff, tr.lengths, labels, F, max_len, args.steps, args.batch, args.lr,
-                   args.temperature, log=log) if args.steps > 0 else []
+                   args.temperature, log=log, mine_every=args.mine_every, hard=args.hard if args.mine_every else 0,
+                   match=wl.match, mismatch=wl.mismatch, K=args.K) if args.steps > 0 else []
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     if args.checkpoint:
         prop.save(args.checkpoint)
-    t0 = time.perf_counter()
-    prop.build_index(g, max_len)
-    torch.cuda.synchronize()
-    index_s = time.perf_counter() - t0
-    d_eseq, d_eoff = _dev(torch, ev.seq), _dev(torch, ev.offsets)
-    exhaustive_labels(torch, g, d_eseq, d_eoff, ev.count, max_len, wl.match, wl.mismatch)  # warm-up
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    ex = exhaustive_labels(torch, g, d_eseq, d_eoff, ev.count, max_len, wl.match, wl.mismatch)
-    ex_ms = (time.perf_counter() - t0) * 1e3
+    g.close()
+    del d_tseq, d_toff
+
     taus = [float(x) for x in args.taus.split(",")]
-    res = evaluate(torch, prop, g, d_eseq, d_eoff, ev.count, max_len, wl.match, wl.mismatch, args.K, taus, ex, ex_ms)
+    evals = []
+    for spec in args.evals.split(","):
+        ewl, eg = _genome_for(gen, spec)
+        ev = gen.make_reads(eg, dataclasses.replace(rspec, count=args.eval_reads), ewl.seed * 7 + 2)
+        half = ev.count // 2
+        sets = [ev.subset(np.arange(0, half)), ev.subset(np.arange(half, ev.count))]
+        g = mss_load_genome(eg, frag_len=F, max_read_len=max_len)
+        NF = g.info()["num_frags"]
+        t0 = time.perf_counter()
+        prop.build_index(g, max_len)
+        torch.cuda.synchronize()
+        index_s = time.perf_counter() - t0
+        rows = []
+        for part in sets:
+            d_eseq, d_eoff = _dev(torch, part.seq), _dev(torch, part.offsets)
+            exhaustive_labels(torch, g, d_eseq, d_eoff, part.count, max_len, ewl.match, ewl.mismatch)  # warm-up
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ex = exhaustive_labels(torch, g, d_eseq, d_eoff, part.count, max_len, ewl.match, ewl.mismatch)
+            ex_ms = (time.perf_counter() - t0) * 1e3
+            rows.append((part, d_eseq, d_eoff, ex, ex_ms))
+        # tau chosen on the first half, reported on the second
+        part, d_eseq, d_eoff, ex, ex_ms = rows[0]
+        val = evaluate(torch, prop, g, d_eseq, d_eoff, part.count, max_len, ewl.match, ewl.mismatch, args.K, taus, ex,
+                       ex_ms)
+        tau = pick_tau(val)
+        part, d_eseq, d_eoff, ex, ex_ms = rows[1]
+        test = evaluate(torch, prop, g, d_eseq, d_eoff, part.count, max_len, ewl.match, ewl.mismatch, args.K,
+                        sorted(set([-1e30, tau])), ex, ex_ms)
+        evals.append({"genome": ewl.name, "genome_bp": int(eg.shape[0]), "num_frags": int(NF),
+                      "index_s": round(index_s, 2), "eval_reads": part.count,
+                      "exhaustive_reads_per_s": round(part.count / (ex_ms / 1e3), 1),
+                      "tau_chosen_on_validation": tau, "validation": val, "test": test})
+        log(json.dumps(evals[-1]))
+        g.close()
     line = {"metric": "learned proposal + exact rescoring vs exhaustive scan (top-1 agreement, recall, speedup)",
-            "workload": wl.name, "genome_bp": int(genome.shape[0]), "frag_len": F, "num_frags": int(NF),
-            "train_reads": tr.count, "train_steps": args.steps, "batch": args.batch,
+            "train_genome": wl.name, "train_genome_bp": int(genome.shape[0]), "frag_len": F,
+            "read_shape": args.read_shape, "train_reads": tr.count, "train_steps": args.steps, "batch": args.batch,
+            "mine_every": args.mine_every, "hard": args.hard if args.mine_every else 0,
             "loss_first": round(losses[0], 4) if losses else None,
             "loss_last": round(float(np.mean(losses[-20:])), 4) if losses else None,
             "loss_curve": [round(float(np.mean(c)), 4) for c in np.array_split(np.asarray(losses), min(10, len(losses)))]
             if losses else [],
-            "label_s": round(label_s, 2), "train_s": round(train_s, 2), "index_s": round(index_s, 2),
-            "eval_reads": ev.count, "exhaustive_ms": round(ex_ms, 1),
-            "exhaustive_reads_per_s": round(ev.count / (ex_ms / 1e3), 1), "K": args.K, "results": res}
+            "label_s": round(label_s, 2), "train_s": round(train_s, 2), "K": args.K, "evals": evals}
     print(json.dumps(line), flush=True)
     prop.close()
-    g.close()
 
 
 if __name__ == "__main__":

@@ -261,16 +261,57 @@ def test_autotune_keeps_results(mss):
 @pytest.mark.parametrize("world", [2, 3])
 def test_genome_sharding_on_gpu_equals_unsharded(mss, world):
     """Genome shards mapped one after another on this GPU and merged (the exchange emulated in
-    memory) give the unsharded result bit for bit."""
+    memory) give the oracle's whole-genome result bit for bit, including a planted tie between
+    a fragment's owner and the partial copy of it on the rank before."""
     from paper_1403_2136_gb300 import shard
     wl = gen.scaled(gen.workloads()["bact-4.6M"], genome_len=300_000, reads=60)
     genome, reads = gen.materialize(wl)
     ml = int(np.diff(reads.offsets).max())
-    got = shard.map_sharded_local(genome, 2048, reads.seq, reads.offsets, 5, -4, world, ml)
-    g = mss.mss_load_genome(genome, frag_len=2048, max_read_len=ml)
-    want = mss.mss_map_reads(g, reads.seq, reads.offsets, 5, -4)
+    # plant a tie across rank 0's border: a read whose reverse complement lies in the partial
+    # view rank 0 has of the first fragment of rank 1, and whose forward copy lies further
+    # into that fragment (outside the view): the owner's + strand copy must win
+    genome = genome.copy()
+    F = 2048
+    f1 = shard.shard_bounds(genome.shape[0], F, world, 0, ml)[1]
+    rng = np.random.default_rng(world)
+    read = np.frombuffer(b"ACGT", np.uint8)[rng.integers(0, 4, 100)].copy()
+    genome[f1 * F + 600:f1 * F + 700] = read
+    genome[f1 * F + 2:f1 * F + 102] = np.frombuffer(read.tobytes()[::-1].translate(bytes.maketrans(b"ACGT", b"TGCA")),
+                                                     np.uint8)
+    seq = np.concatenate([reads.seq, read])
+    off = np.concatenate([reads.offsets, [reads.offsets[-1] + 100]]).astype(np.int64)
+    got = shard.map_sharded_local(genome, F, seq, off, 5, -4, world, ml)
+    g = mss.mss_load_genome(genome, frag_len=F, max_read_len=ml)
+    unsharded = mss.mss_map_reads(g, seq, off, 5, -4)
     g.close()
-    assert_hits_equal(got, want, f"{world} GPU shards")
+    want, _, _ = oracle_map(genome, F, seq, off, 5, -4, procs=cpu_count())
+    assert_hits_equal(unsharded, want, "unsharded GPU vs oracle")
+    assert_hits_equal(got, want, f"{world} GPU shards vs oracle")
+    last = want[-1]
+    assert (int(last["best_frag"]), int(last["best_score"]), int(last["offset"]), int(last["strand"])) == \
+        (f1, 500, f1 * F + 600, 0)
+
+
+def test_bounded_wait_gives_up_and_reports_timeout(mss):
+    """A bounded device wait that runs out (an mbarrier phase nothing completes, 5 ms limit)
+    comes back as MSS_ETIMEOUT from the synchronising call; the error word is cleared and the
+    context still maps reads bit-exactly afterwards."""
+    import time
+    wl = gen.scaled(gen.workloads()["tiny-50k"], genome_len=20_000, reads=8)
+    genome, reads = gen.materialize(wl)
+    g = mss.mss_load_genome(genome, frag_len=wl.frag_len, max_read_len=100)
+    t0 = time.perf_counter()
+    st = mss.mss_check_wait_timeout(g, 5000)
+    dt = time.perf_counter() - t0
+    assert st == mss.MSS_ETIMEOUT, st
+    assert dt >= 0.004, dt
+    mss.mss_sync(g)                                  # cleared: no error left behind
+    assert mss.mss_check_wait_timeout(g, 0) == mss.MSS_EINVAL
+    assert mss.mss_check_wait_timeout(g, 2_000_000) == mss.MSS_EINVAL
+    hits = mss.mss_map_reads(g, reads.seq, reads.offsets, wl.match, wl.mismatch)
+    want, _, _ = oracle.map_batch(genome, wl.frag_len, reads.seq, reads.offsets, wl.match, wl.mismatch)
+    assert_hits_equal(hits, want, "after the wait self-check")
+    g.close()
 
 
 # ---------------------------------------------------------------- MaxSSmap_fast (read step 2)

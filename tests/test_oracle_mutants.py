@@ -53,6 +53,8 @@ MUTANTS = {
     "lowercase_a_invalid": ("case 'A': case 'a': return 0;", "case 'A': return 0;"),
     # strand tie rule reversed (reverse complement before the read)
     "strand_ties_reversed": ("for (int32_t sg = 0; sg < 2; ++sg) {", "for (int32_t sg = 1; sg >= 0; --sg) {"),
+    # base qualities: phase two's gap costs left unscaled (scores in 1/scale units, gaps not)
+    "pssm_gap_unscaled": ("W, gap_open * scale, gap_extend * scale,", "W, gap_open, gap_extend,"),
     # neighbour rule: only the right neighbour excluded
     "neighbour_rule_one_side": ("if (exclude_neighbors && (f == b1 - 1 || f == b1 + 1)) continue;",
                                 "if (exclude_neighbors && (f == b1 + 1)) continue;"),

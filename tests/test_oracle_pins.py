@@ -622,3 +622,23 @@ def test_neighbour_exclusion_bruteforce():
         s1 = fs[b1]
         rep = 1 if (s1 == 0 or 10 * s2 >= 9 * s1) else 0
         assert got == (b1, b2, s1, s2, plain[4], plain[5], rep), (genome, F, read)
+
+
+def test_pssm_batch_gap_costs_are_scaled():
+    """Phase two with base qualities is in units of 1/scale, so its gap costs are scaled too
+    ("Incorporating base qualities": match * x and mismatch * x / 3, here times scale 4).
+    Hand-worked case: a 20-base read made of genome[60:70] + genome[72:82] (two genome bases
+    deleted), every base at quality 'I' (Q 40, x = 0.9999): a match scores round(4 * 5 * x) = 20,
+    and the best glocal alignment is 20 matches with one 2-base gap in the read:
+    20 * 20 + 4 * (-10) + 4 * (-1) = 356.  With unscaled gaps it would be 389."""
+    rng = np.random.default_rng(1403)
+    genome = np.frombuffer(b"ACGT", np.uint8)[rng.integers(0, 4, 200)].copy()
+    read = np.concatenate([genome[60:70], genome[72:82]])
+    off = np.array([0, 20], dtype=np.int64)
+    quals = np.full(20, ord("I"), dtype=np.uint8)
+    assert oracle.pssm_scores(ord("I"), 5, -4, 4) == (20, -5)
+    hits, alns, cig = oracle.map_batch(genome, 200, read, off, 5, -4, nw=(5, -4, -10, -1, 32), quals=quals, scale=4)
+    assert int(hits["best_score"][0]) >= 10 * 20          # one half of the read lies on one diagonal
+    assert int(alns["score"][0]) == 20 * 20 + 4 * (-10) + 4 * (-1) == 356
+    assert cig[0] == "10M2D10M", cig[0]
+    assert int(alns["gstart"][0]) == 60 and int(alns["gend"][0]) == 82
