@@ -62,6 +62,10 @@ def parse():
     ap.add_argument("--autotune-reads", type=int, default=256)
     ap.add_argument("--read-step", type=int, default=1, choices=[1, 2],
                     help="2: MaxSSmap_fast (every other read base in phase one)")
+    ap.add_argument("--no-proposal", action="store_true", help="skip the learned-proposal measurement")
+    ap.add_argument("--prop-train-reads", type=int, default=20_000)
+    ap.add_argument("--prop-steps", type=int, default=400)
+    ap.add_argument("--prop-eval-reads", type=int, default=8_000)
     return ap.parse_args()
 
 
@@ -92,9 +96,9 @@ def batches(seq, off, batch: int):
 
 # DRAM bytes (read + write) of one k_scan launch of the default workload (bact-4.6M, one
 # 50,000-read batch, F = 2048, read step 1), from an ncu capture of that launch with
-# dram__bytes_read.sum and dram__bytes_write.sum (one pass); None until captured for the
-# kernel as built.  Other workloads report no traffic.
-SCAN_DRAM_BYTES_DEFAULT = None
+# dram__bytes_read.sum and dram__bytes_write.sum (one pass; the command and the figures are in
+# profiles/launches_bact-4.6M_50k-read-batch.md).  Other workloads report no traffic.
+SCAN_DRAM_BYTES_DEFAULT = 8.895232e6
 
 
 def workload_config(wl, genome, lengths, F: int, args, world: int = 1) -> dict:
@@ -246,6 +250,83 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# ------------------------------------------------------------------------------- learned proposal
+def measure_proposal(torch, mss, g, wl, genome, max_len, args, stream) -> dict:
+    """The second half of the metric: learned proposal + exact rescoring (+ exhaustive fallback
+    below a threshold) against the exhaustive scan, on held-out reads of the workload's recipe
+    drawn from the same genome.  The model is trained here on exhaustive-scan labels of
+    separate training reads; the threshold is chosen on a validation set (the smallest one
+    that reaches 99.5% top-1 agreement), then reads/s and agreement are measured on a test set.
+    Outside the timed region of the main metric."""
+    from paper_1403_2136_gb300.proposal import evaluate, exhaustive_labels, pick_tau, train
+    K = 64
+    rs = wl.reads
+    def draw(n, seed):
+        per = [max(1, n * r.count // sum(x.count for x in rs)) for r in rs]
+        parts = [gen.make_reads(genome, gen.ReadSpec(**{**r.__dict__, "count": c}), seed + i)
+                 for i, (r, c) in enumerate(zip(rs, per))]
+        return gen.concat_reads(parts)
+    tr = draw(args.prop_train_reads, wl.seed * 97 + 11)
+    va = draw(args.prop_eval_reads // 2, wl.seed * 97 + 23)
+    te = draw(args.prop_eval_reads, wl.seed * 97 + 37)
+    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()  # noqa: E731
+    d_tseq, d_toff = dev(tr.seq), dev(tr.offsets)
+    t0 = time.perf_counter()
+    labels = exhaustive_labels(torch, g, d_tseq, d_toff, tr.count, max_len, wl.match, wl.mismatch)
+    label_s = time.perf_counter() - t0
+    prop = mss.Proposal(seed=1)
+    t0 = time.perf_counter()
+    losses = train(torch, prop, g, d_tseq, d_toff, tr.lengths, labels, wl.frag_len, max_len, args.prop_steps, 256,
+                   2e-3, 0.05, log=None)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    prop.build_index(g, max_len)
+    taus = [-1e30, 0.3, 0.4, 0.5, 0.6, 0.7, 0.8, 0.9, 1.01]
+    d_vseq, d_voff = dev(va.seq), dev(va.offsets)
+    ex_v = exhaustive_labels(torch, g, d_vseq, d_voff, va.count, max_len, wl.match, wl.mismatch)
+    val = evaluate(torch, prop, g, d_vseq, d_voff, va.count, max_len, wl.match, wl.mismatch, K, taus, ex_v, 1.0)
+    tau = pick_tau(val)
+    d_eseq, d_eoff = dev(te.seq), dev(te.offsets)
+    exhaustive_labels(torch, g, d_eseq, d_eoff, te.count, max_len, wl.match, wl.mismatch)   # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ex = exhaustive_labels(torch, g, d_eseq, d_eoff, te.count, max_len, wl.match, wl.mismatch)
+    ex_ms = (time.perf_counter() - t0) * 1e3
+    res = {r["tau"]: r for r in evaluate(torch, prop, g, d_eseq, d_eoff, te.count, max_len, wl.match, wl.mismatch, K,
+                                         sorted({-1e30, tau}), ex, ex_ms)}
+    chosen, free = res[tau], res[-1e30]
+    # end to end: reads uploaded from pinned host memory, hits read back, inside the timing
+    h_seq, h_off = torch.from_numpy(te.seq).pin_memory(), torch.from_numpy(te.offsets).pin_memory()
+    h_hits = torch.empty(te.count * 32, dtype=torch.uint8).pin_memory()
+    d_out = torch.empty(te.count * 32, dtype=torch.uint8, device="cuda")
+    reps = 3
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        d_eseq.copy_(h_seq, non_blocking=True)
+        d_eoff.copy_(h_off, non_blocking=True)
+        prop.map_reads(g, d_eseq, d_eoff, te.count, max_len, wl.match, wl.mismatch, K, tau, d_out)
+        h_hits.copy_(d_out)
+    torch.cuda.synchronize()
+    te_s = (time.perf_counter() - t0) / reps
+    prop.close()
+    return {"workload": f"{wl.name.split(':')[0]} genome, held-out reads of its recipe", "K": K, "tau": tau,
+            "tau_rule": "smallest threshold with >= 99.5% top-1 agreement on a validation set",
+            "train": {"reads": tr.count, "steps": args.prop_steps, "batch": 256, "label_s": round(label_s, 2),
+                      "train_s": round(train_s, 2), "loss_first": round(losses[0], 4) if losses else None,
+                      "loss_last": round(float(np.mean(losses[-20:])), 4) if losses else None},
+            "validation_reads": va.count, "eval_reads": te.count,
+            "reads_per_s": chosen["reads_per_s"], "exhaustive_reads_per_s": round(te.count / (ex_ms / 1e3), 1),
+            "speedup_vs_exhaustive": chosen["speedup_vs_exhaustive"],
+            "top1_agreement": chosen["top1_agreement"], "recall_at_64": chosen["recall_at_64"],
+            "fallback_fraction": round(chosen["fallback_reads"] / te.count, 5),
+            "changed_mappings": chosen["changed_mappings"],
+            "no_fallback": {"reads_per_s": free["reads_per_s"], "top1_agreement": free["top1_agreement"],
+                            "recall_at_64": free["recall_at_64"], "speedup_vs_exhaustive": free["speedup_vs_exhaustive"]},
+            "e2e": {"reads_per_s": round(te.count / te_s, 1), "h2d_bytes_per_step": int(te.seq.nbytes + te.offsets.nbytes),
+                    "d2h_bytes_per_step": int(te.count * 32)}}
+
+
 # ------------------------------------------------------------------------------- GPU arm
 def peak_nominal_tcups(sms: int, clk_mhz: float) -> float:
     """Nominal two-pipe figure: 2 int16 ops per cell (add-relu, max); packed 16-bit x2 work runs
@@ -255,13 +336,20 @@ def peak_nominal_tcups(sms: int, clk_mhz: float) -> float:
 
 
 def peak_measured_tcups(probe, sms: int, clk_mhz: float):
-    """Measured two-pipe figure: the library's pipe probe with one packed int16 DPX add-max and
-    one packed f16 FMA-relu per chain step (both pipes busy) gives warp-instructions per SM
-    clock; each packed warp-instruction is 64 lane operations, a cell needs 2, so cells per SM
-    clock = rate x 32."""
+    """Measured two-pipe figure: the library's probe with PRMT (integer pipe) and f16 FMA-relu
+    (FMA pipe) interleaved keeps both 16-lane pipes busy; each packed warp-instruction is 64
+    lane operations and a cell needs 2, so cells per SM clock = rate x 32."""
     if not probe:
         return None
-    return probe[2] * 32 * sms * clk_mhz * 1e6 / 1e12
+    return probe["prmt_and_fma_relu"] * 32 * sms * clk_mhz * 1e6 / 1e12
+
+
+def mix_ceiling_tcups(probe, sms: int, clk_mhz: float):
+    """The scan's own instruction mix measured in isolation (2 PRMT + 2 f16 FMA-relu + 1 three-
+    input max per 2 lane pairs of 32 threads x 2 cells = 128 cells per 5 warp-instructions)."""
+    if not probe:
+        return None
+    return probe["scan_mix"] * 128 / 5 * sms * clk_mhz * 1e6 / 1e12
 
 
 def scan_lanes(max_len: int, match: int, mismatch: int, variant: int) -> str:
@@ -283,16 +371,17 @@ def bench_line(*, gcups, t, world, args, reads_s, e2e, launches, sms, probe, max
     peak = measured if measured else nominal
     # the integer/DPX pipe alone, measured by the same probe: warp-instructions per SM clock x
     # 32 threads x 2 lanes / 2 ops per cell
-    dpx_only = probe[0] * 32 * sms * clk_mhz * 1e6 / 1e12 if probe else None
+    dpx_only = probe["dpx_add_max"] * 32 * sms * clk_mhz * 1e6 / 1e12 if probe else None
+    mix = mix_ceiling_tcups(probe, sms, clk_mhz)
     lanes = scan_lanes(max_len, wl.match, wl.mismatch, tune["variant"])
     default_run = (wl.name == gen.workloads()[args.workload].name and args.workload == "bact-4.6M"
                    and args.read_step == 1 and not args.autotune and frag_len == 2048 and args.batch == 50_000)
     traffic = SCAN_DRAM_BYTES_DEFAULT if default_run else None
     scan_mean_ms = statistics.mean(scan_ms)
     achieved = cells_timed / (sum(scan_ms) * 1e-3) / 1e12
-    src = (f"measured: pipe probe with one packed int16 DPX add-max and one packed f16 FMA-relu per step "
-           f"(both 16-lane pipes busy): {probe[2]:.3f} warp-instructions per SM clock x 32 cells x {sms} SMs "
-           f"x {clk_mhz:.0f} MHz" if measured else
+    src = (f"measured: pipe probe with PRMT (integer pipe) and packed f16 FMA-relu (FMA pipe) interleaved, "
+           f"both 16-lane pipes busy: {probe['prmt_and_fma_relu']:.3f} warp-instructions per SM clock x 32 cells "
+           f"x {sms} SMs x {clk_mhz:.0f} MHz" if measured else
            f"nominal: {sms} SMs x 4 sub-partitions x 32 cells/clk x {clk_mhz:.0f} MHz")
     return {
         "metric": METRIC, "value": round(gcups, 3), "unit": "GCUPS", "n_gpus": world, "steps": args.steps,
@@ -311,7 +400,10 @@ def bench_line(*, gcups, t, world, args, reads_s, e2e, launches, sms, probe, max
                      "peak_nominal": round(nominal, 3), "frac_of_nominal": round(achieved / nominal, 4),
                      "scan_ms_per_step": round(scan_mean_ms, 3),
                      "peak_dpx_pipe_only": round(dpx_only, 3) if dpx_only else None,
-                     "frac_of_dpx_pipe_only": round(achieved / dpx_only, 4) if dpx_only else None},
+                     "frac_of_dpx_pipe_only": round(achieved / dpx_only, 4) if dpx_only else None,
+                     "mix_ceiling": round(mix, 3) if mix else None,
+                     "frac_of_mix_ceiling": round(achieved / mix, 4) if mix else None,
+                     "probe_warp_instr_per_sm_clk": {k: round(v, 4) for k, v in probe.items()} if probe else None},
         "cpu_baseline": cpu,
         "clocks": clk,
     }
@@ -460,12 +552,21 @@ def main():
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "reads_per_s": round(e_reads * world / te, 1)}
 
+    prop = None
+    if rank == 0 and not args.no_proposal:
+        # on the default stream: the proposal helpers pass no stream to the library, so torch's
+        # copies and the library's launches are ordered on the same stream
+        torch.cuda.synchronize(dev)
+        prop = measure_proposal(torch, mss, g, wl, genome, max_len, args, None)
+
     if rank == 0:
         line = bench_line(
             gcups=gcups, t=t, world=world, args=args, reads_s=reads_s, e2e=e2e, launches=launches,
             sms=props.multi_processor_count, probe=probe, max_len=max_len, wl=wl, genome=genome,
             lengths=lengths, frag_len=info["frag_len"], tune=mss.mss_get_tune(g), tuned=tuned,
             cells_timed=cells_timed, scan_ms=scan_ms, cpu=cpu, clk=clk)
+        if prop is not None:
+            line["proposal"] = prop
         print(json.dumps(line), flush=True)
     g.close()
     if world > 1:

@@ -184,7 +184,7 @@ def make_reads(genome: np.ndarray, spec: ReadSpec, seed: int, positions: bool = 
         if rc != 0:
             raise RuntimeError(f"gen_reads failed ({rc})")
         parts.append(Reads(seq, offs, ts, st, ns, ng, rel))
-    return _concat(parts)
+    return concat_reads(parts)
 
 
 @dataclass
@@ -253,7 +253,7 @@ def scaled(wl: Workload, genome_len: int | None = None, reads: int | None = None
                     wl.match, wl.mismatch, wl.nw, wl.seed, wl.notes)
 
 
-def _concat(parts: list) -> Reads:
+def concat_reads(parts: list) -> Reads:
     if len(parts) == 1:
         return parts[0]
     R = sum(p.count for p in parts)
@@ -271,7 +271,7 @@ def read_set(wl: Workload, genome: np.ndarray, rank: int = 0, positions: bool = 
     """All reads of a workload in order (its ReadSpecs one after another), drawn for one rank:
     rank 0 gives the reads of ``materialize``; other ranks get other seeds.  positions: also
     record every base's true genome position (``Reads.true_rel``)."""
-    return _concat([make_reads(genome, rs, wl.seed * 31 + i + 1000003 * rank, positions)
+    return concat_reads([make_reads(genome, rs, wl.seed * 31 + i + 1000003 * rank, positions)
                     for i, rs in enumerate(wl.reads)])
 
 

@@ -239,11 +239,17 @@ MSS_API int64_t mss_launch_count(const mss_ctx* ctx);
 MSS_API mss_status mss_genome_codes(const mss_ctx* ctx, int64_t start, int64_t n, uint8_t* out);
 
 /*
- * Throughput probe of the two 16-bit SIMD pipes used by the scan: warp-instructions per SM
- * clock of (0) packed-int16 DPX add-max, (1) f16x2 FMA with relu, (2) both interleaved.
- * clk_mhz receives the SM clock the device reports.  Used for the roofline denominator.
+ * Throughput probes of the packed 16-bit instructions the scan uses, in warp-instructions per
+ * SM clock (at the clock the device reports as its maximum), each from 16 independent chains
+ * per thread: rates[0] packed int16 DPX add-max, [1] f16x2 FMA with relu, [2] PRMT and f16x2
+ * FMA-relu interleaved (the integer and FMA pipes both busy: the two-pipe peak of the scan's
+ * roofline), [3] PRMT, [4] three-input packed int16 max, [5] the scan's own mix (2 PRMT +
+ * 2 FMA-relu + 1 three-input max per two lane pairs), [6] DPX add-max and FMA-relu
+ * interleaved.  The first min(n_rates, 7) slots are filled; clk_mhz receives the clock used.
+ * Allocates a small device buffer for the duration of the call.  MSS_EINVAL for null
+ * pointers or n_rates < 1, MSS_ECUDA on a CUDA failure.
  */
-MSS_API mss_status mss_probe_pipes(double* rates3, double* clk_mhz);
+MSS_API mss_status mss_probe_pipes(double* rates, int32_t n_rates, double* clk_mhz);
 
 /*
  * Self-check of failure detection (a property of this library, not of the paper's method):

@@ -109,7 +109,7 @@ def load_library(path: str = LIB_PATH):
         "mss_scan_time_ms": ([P, ctypes.POINTER(ctypes.c_float)], i32),
         "mss_launch_count": ([P], i64),
         "mss_genome_codes": ([P, i64, i64, P], i32),
-        "mss_probe_pipes": ([ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], i32),
+        "mss_probe_pipes": ([ctypes.POINTER(ctypes.c_double), i32, ctypes.POINTER(ctypes.c_double)], i32),
         "mss_check_wait_timeout": ([P, ctypes.c_uint32, P], i32),
         "mss_prop_create": ([ctypes.POINTER(P), ctypes.c_uint64, P], i32),
         "mss_prop_free": ([P], None),
@@ -399,12 +399,16 @@ def mss_genome_codes(g: Genome, start: int, n: int) -> np.ndarray:
     return out
 
 
+PROBE_MODES = ("dpx_add_max", "fma_relu", "prmt_and_fma_relu", "prmt", "max3", "scan_mix", "dpx_and_fma_relu")
+
+
 def mss_probe_pipes():
-    """(dpx, fma, both) warp-instructions per SM clock, and the reported SM clock in MHz."""
-    r = (ctypes.c_double * 3)()
+    """Warp-instructions per SM clock of the probes (dict keyed by PROBE_MODES) and the SM clock
+    in MHz the rates are counted at."""
+    r = (ctypes.c_double * len(PROBE_MODES))()
     clk = ctypes.c_double()
-    _check(load_library().mss_probe_pipes(r, ctypes.byref(clk)), "mss_probe_pipes")
-    return list(r), clk.value
+    _check(load_library().mss_probe_pipes(r, len(PROBE_MODES), ctypes.byref(clk)), "mss_probe_pipes")
+    return dict(zip(PROBE_MODES, list(r))), clk.value
 
 
 def mss_check_wait_timeout(g: Genome, limit_us: int = 2000, stream=None) -> int:

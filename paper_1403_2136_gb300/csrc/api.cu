@@ -845,9 +845,9 @@ mss_status mss_genome_codes(const mss_ctx* c, int64_t start, int64_t n, uint8_t*
   return MSS_OK;
 }
 
-mss_status mss_probe_pipes(double* rates3, double* clk_mhz) {
-  if (!rates3 || !clk_mhz) return fail(MSS_EINVAL, "null argument");
-  CK(probe_pipes(rates3, clk_mhz), "pipe probe");
+mss_status mss_probe_pipes(double* rates, int32_t n_rates, double* clk_mhz) {
+  if (!rates || !clk_mhz || n_rates < 1) return fail(MSS_EINVAL, "null argument or no rate slots");
+  CK(probe_pipes(rates, n_rates, clk_mhz), "pipe probe");
   return MSS_OK;
 }
 

@@ -126,7 +126,7 @@ struct NwArgs {
 int64_t nw_scratch_per_warp(int32_t max_len, int32_t band);
 cudaError_t launch_nw(const NwArgs& a, int grid_warps, cudaStream_t s);
 
-cudaError_t probe_pipes(double* rates3, double* clk_mhz);
+cudaError_t probe_pipes(double* rates, int n, double* clk_mhz);
 cudaError_t launch_wait_selfcheck(int32_t* err, uint64_t limit_ns, cudaStream_t s);
 // f16 bit pattern of a small integer; whether the f16 lanes are exact for these scores
 uint32_t int_to_f16_bits(int32_t x);

@@ -160,7 +160,8 @@ def main(argv=None):
     ap.add_argument("--hard", type=int, default=2, help="hard negatives per read from the model's own top K")
     ap.add_argument("--K", type=int, default=64)
     ap.add_argument("--evals", default="chrom-230M@23000000",
-                    help="comma-separated evaluation genomes name[@length] (held-out reads of the read shape)")
+                    help="comma-separated evaluation genomes name[@length][:reads] (held-out reads of the read "
+                         "shape; the read count overrides --eval-reads for that genome)")
     ap.add_argument("--eval-reads", type=int, default=20_000, help="held-out reads per genome (half choose tau)")
     ap.add_argument("--taus", type=str, default="-1e30,0.3,0.4,0.5,0.6,0.7,0.8,0.9",
                     help="comma-separated; pass as --taus=...")
@@ -197,8 +198,9 @@ def main(argv=None):
     taus = [float(x) for x in args.taus.split(",")]
     evals = []
     for spec in args.evals.split(","):
+        spec, _, nr = spec.partition(":")
         ewl, eg = _genome_for(gen, spec)
-        ev = gen.make_reads(eg, dataclasses.replace(rspec, count=args.eval_reads), ewl.seed * 7 + 2)
+        ev = gen.make_reads(eg, dataclasses.replace(rspec, count=int(nr) if nr else args.eval_reads), ewl.seed * 7 + 2)
         half = ev.count // 2
         sets = [ev.subset(np.arange(0, half)), ev.subset(np.arange(half, ev.count))]
         g = mss_load_genome(eg, frag_len=F, max_read_len=max_len)

@@ -22,7 +22,7 @@ def _line(monkeypatch, variant=-1, workload="bact-4.6M"):
     return bench.bench_line(
         gcups=20000.0, t=68.6, world=1, args=args, reads_s=17500.0,
         e2e={"value": 19900.0, "unit": "GCUPS", "h2d_bytes_per_step": 10, "d2h_bytes_per_step": 20},
-        launches=18, sms=152, probe=(1.97, 3.9, 3.9), max_len=int(lengths.max()), wl=wl, genome=genome,
+        launches=18, sms=152, probe={"dpx_add_max": 1.97, "fma_relu": 1.9, "prmt_and_fma_relu": 3.5, "prmt": 1.9, "max3": 1.9, "scan_mix": 2.5, "dpx_and_fma_relu": 2.3}, max_len=int(lengths.max()), wl=wl, genome=genome,
         lengths=lengths, frag_len=wl.frag_len, tune=tune, tuned=None, cells_timed=3 * cells, scan_ms=[22748.0] * 3,
         cpu={"value": 7.4, "unit": "GCUPS", "cores": 16, "kind": "oracle", "sample": "32 reads"},
         clk={"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 300})
@@ -41,8 +41,9 @@ def test_line_has_the_contract_keys(monkeypatch):
         assert k in r, k
     assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-3
     assert r["traffic"] == bench.SCAN_DRAM_BYTES_DEFAULT      # default workload: the captured bytes
-    # the measured both-pipe probe rate (3.9 warp-instructions per SM clock) x 32 cells
-    assert abs(r["peak"] - 3.9 * 32 * 152 * 2070e6 / 1e12) < 1e-3
+    # the measured both-pipe probe rate (3.5 warp-instructions per SM clock) x 32 cells
+    assert abs(r["peak"] - 3.5 * 32 * 152 * 2070e6 / 1e12) < 1e-3
+    assert abs(r["mix_ceiling"] - 2.5 * 128 / 5 * 152 * 2070e6 / 1e12) < 1e-3
     assert abs(r["peak_nominal"] - 152 * 4 * 32 * 2070e6 / 1e12) < 1e-3
     assert abs(r["achieved"] - 3 * bench.cells_of(np.array([100] * 4 + [150] * 4), 4_600_000, 2048) /
                (3 * 22.748) / 1e12) < 1e-3

@@ -6,7 +6,8 @@
   over the batch (both lengths, all three divergence levels) are compared field by field with
   the oracle: all seven hit fields, and the NW score, span and CIGAR.
 * Genome positions beyond 2^31: the 2.4 Gbp genome of the ancient-DNA workload with reads
-  drawn from its last 100 Mbp.  Checked by what the oracle can compute one read at a time:
+  drawn from its last 100 Mbp (the workload's lengths, low divergence so that they map where
+  they were drawn).  Checked by what the oracle can compute one read at a time:
   the reported best and second fragment scores are the oracle's S(f) of those fragments, the
   offset and strand attain the best score, the repeat flag follows from the scores, the
   fragment the read was drawn from scores at most the best (and at most the second when it
@@ -105,7 +106,9 @@ def test_genome_offsets_beyond_2_31(mss):
     G = int(genome.shape[0])
     base = G - 100_000_000
     assert base > 2**31
-    rs = gen.ReadSpec(96, lognormal=(45, 0.35, 25, 80), sub_levels=((0.15, 0.25),), deam_rate=0.30, deam_len=5)
+    # the workload's read lengths at low divergence, so that nearly every read maps where it
+    # was drawn and the offsets checked lie beyond 2^31
+    rs = gen.ReadSpec(96, lognormal=(45, 0.35, 25, 80), sub_levels=((0.0, 0.05),), gap_mode=0)
     reads = gen.make_reads(genome[base:], rs, wl.seed * 37)
     max_len = int(reads.lengths.max())
     F = wl.frag_len
@@ -114,7 +117,7 @@ def test_genome_offsets_beyond_2_31(mss):
     g.close()
     nm, nmm, go, ge, W = wl.nw
     checked_high = 0
-    for i in range(0, reads.count, 4):
+    for i in range(0, reads.count, 2):
         h = hits[i]
         read = reads.read(i)
         s1 = _frag_score(genome, F, read, int(h["best_frag"]))
@@ -144,4 +147,4 @@ def test_genome_offsets_beyond_2_31(mss):
             (a[0], a[1] + lo if a[1] >= 0 else a[1], a[2] + lo if a[2] >= 0 else a[2]), i
         assert cig[i] == a[3]
         checked_high += d >= 2**31
-    assert checked_high >= reads.count // 8, checked_high
+    assert checked_high >= reads.count // 4, checked_high      # of the 48 reads checked
