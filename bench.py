@@ -363,9 +363,11 @@ def scan_lanes(max_len: int, match: int, mismatch: int, variant: int) -> str:
 
 
 def bench_line(*, gcups, t, world, args, reads_s, e2e, launches, sms, probe, max_len, wl, genome, lengths,
-               frag_len, tune, tuned, cells_timed, scan_ms, cpu, clk) -> dict:
-    """The JSON line of the GPU arm from the measured values (no device work here)."""
-    clk_mhz = 2070.0
+               frag_len, tune, tuned, cells_timed, scan_ms, cpu, clk, probe_mhz=None) -> dict:
+    """The JSON line of the GPU arm from the measured values (no device work here).  The probe
+    rates are per SM clock at probe_mhz, the clock the library counts them at (the device's
+    maximum SM clock, which the sampled clocks show the GPU running at under load)."""
+    clk_mhz = probe_mhz or 2070.0
     nominal = peak_nominal_tcups(sms, clk_mhz)
     measured = peak_measured_tcups(probe, sms, clk_mhz)
     peak = measured if measured else nominal
@@ -485,7 +487,8 @@ def main():
         for i in range(args.warmup):
             step(i % nb)
         mss.mss_sync(g, stream=stream)
-        probe = mss.mss_probe_pipes()[0] if rank == 0 else None   # pipe rates, outside the timed region
+        # instruction rates per SM clock and the clock they are counted at, outside the timed region
+        probe, probe_mhz = mss.mss_probe_pipes() if rank == 0 else (None, None)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(args.steps)]
         scan_ms = []
@@ -562,7 +565,7 @@ def main():
     if rank == 0:
         line = bench_line(
             gcups=gcups, t=t, world=world, args=args, reads_s=reads_s, e2e=e2e, launches=launches,
-            sms=props.multi_processor_count, probe=probe, max_len=max_len, wl=wl, genome=genome,
+            sms=props.multi_processor_count, probe=probe, probe_mhz=probe_mhz, max_len=max_len, wl=wl, genome=genome,
             lengths=lengths, frag_len=info["frag_len"], tune=mss.mss_get_tune(g), tuned=tuned,
             cells_timed=cells_timed, scan_ms=scan_ms, cpu=cpu, clk=clk)
         if prop is not None:

@@ -33,6 +33,11 @@
 
 namespace mss {
 
+template <bool B>
+struct BoolTag {
+  static constexpr bool value = B;
+};
+
 // D lane pairs per thread, NT threads, reads up to MAXL bases (selector rows sized for it)
 template <int D, int NT, int MAXL>
 struct ScanGeo {
@@ -296,7 +301,12 @@ __global__ void __launch_bounds__(NT, MINB) k_scan(ScanArgs a) {
         if (PSSM) nnext[v] = reinterpret_cast<const uint4*>(profn)[v];
       }
 
-      for (int k0 = 0; k0 < mpad; k0 += BS) {
+      // whole blocks of BS steps, then the last block cut at the group's longest read: steps
+      // past it would only score padding (mismatches), which lowers H and never raises M
+      const int nfull = nsteps / BS * BS;
+      const int rem = nsteps - nfull;
+      auto block = [&](int k0, auto tail, int nvalid) {
+        constexpr bool kTail = decltype(tail)::value;
         // positions entering the window during this block: p = tid*SPAN + STEP*k0 + D + i,
         // i < D, all in one selector row band and one column; pair j of step k = k0 + u reads
         // position tid*SPAN + STEP*k + j, kept in win[(j + STEP*u) % D] (STEP*k0 is a
@@ -307,6 +317,7 @@ __global__ void __launch_bounds__(NT, MINB) k_scan(ScanArgs a) {
         const uint4* pn = reinterpret_cast<const uint4*>(profn + (k0 + 1) * RQ);
 #pragma unroll
         for (int u = 0; u < BS; ++u) {
+          if (kTail && u >= nvalid) break;  // the same for every thread of the CTA
           uint32_t pw[RQ], nw[RQ];
 #pragma unroll
           for (int v = 0; v < RQ / 4; ++v) {
@@ -339,13 +350,18 @@ __global__ void __launch_bounds__(NT, MINB) k_scan(ScanArgs a) {
 #pragma unroll
           for (int e = 0; e < STEP; ++e) win[(STEP * u + e) % D] = sp[(STEP * u + e) * W];
         }
-      }
-      // mpad is a multiple of BS (even): the last step is odd, so pairs with odd j hold one
-      // value not yet folded
+      };
+      for (int k0 = 0; k0 < nfull; k0 += BS) block(k0, BoolTag<false>{}, BS);
+      if (rem > 0) block(nfull, BoolTag<true>{}, rem);
+      // step u folds into pair j's maximum when u and j differ in parity (blocks have an even
+      // number of steps, so u's parity is the step's): after the last step, the pairs of its
+      // parity hold one value not yet folded
+      const int last_parity = (nsteps - 1) & 1;
 #pragma unroll
       for (int q = 0; q < RQ; ++q)
 #pragma unroll
-        for (int j = 1; j < D; j += 2) M[q][j] = __vimax3_s16x2(M[q][j], H[q][j], 0u);
+        for (int j = 0; j < D; ++j)
+          if ((j & 1) == last_parity) M[q][j] = __vimax3_s16x2(M[q][j], H[q][j], 0u);
 
       // ---- per-fragment maxima of this thread's 2D diagonals
       const int64_t ds = ts + (int64_t)tid * SPAN;

@@ -143,6 +143,63 @@ def pick_tau(rows, target: float = 0.995):
     return min(ok, key=lambda r: r["tau"])["tau"] if ok else max(r["tau"] for r in rows)
 
 
+def at_scale(torch, gen, prop, args, rspec, max_len, F, taus, log):
+    """All --scale-reads reads through the proposal without fallback (top K, exact rescoring),
+    timed; an evenly spaced subsample through the exhaustive scan, timed; agreement and the
+    fallback fraction at each threshold on the subsample (a read below the threshold falls back
+    and then agrees by construction).  Running the fallback for every read of the full set is
+    left out when it would take the exhaustive scan's time (the rate is reported)."""
+    spec, _, _ = args.evals.split(",")[0].partition(":")
+    ewl, eg = _genome_for(gen, spec)
+    t0 = time.perf_counter()
+    ev = gen.make_reads(eg, dataclasses.replace(rspec, count=args.scale_reads), ewl.seed * 7 + 3)
+    log(f"{ev.count} reads drawn in {time.perf_counter() - t0:.1f} s")
+    g = mss_load_genome(eg, frag_len=F, max_read_len=max_len)
+    NF = g.info()["num_frags"]
+    t0 = time.perf_counter()
+    prop.build_index(g, max_len)
+    torch.cuda.synchronize()
+    index_s = time.perf_counter() - t0
+    R, K = ev.count, args.K
+    d_seq, d_off = _dev(torch, ev.seq), _dev(torch, ev.offsets)
+    d_out = torch.empty(R * 32, dtype=torch.uint8, device="cuda")
+    d_cand = torch.empty(R * K, dtype=torch.int32, device="cuda")
+    d_top = torch.empty(R, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    prop.map_reads(g, d_seq, d_off, R, max_len, ewl.match, ewl.mismatch, K, -1e30, d_out, d_cand=d_cand, d_top=d_top)
+    torch.cuda.synchronize()
+    prop_s = time.perf_counter() - t0
+    h = hits_from_bytes(d_out.cpu())
+    top = d_top.cpu().numpy()
+    cand = d_cand.cpu().numpy().reshape(R, K)
+    sub = np.linspace(0, R - 1, min(R, args.subsample)).astype(np.int64)
+    sr = ev.subset(sub)
+    d_sseq, d_soff = _dev(torch, sr.seq), _dev(torch, sr.offsets)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ex = exhaustive_labels(torch, g, d_sseq, d_soff, sr.count, max_len, ewl.match, ewl.mismatch)
+    ex_s = time.perf_counter() - t0
+    g.close()
+    agree = h["best_score"][sub] == ex["best_score"]
+    recall = float(np.mean([ex["best_frag"][i] in cand[s] for i, s in enumerate(sub)]))
+    rows = []
+    ex_rate = sr.count / ex_s
+    for tau in taus:
+        fb = top[sub] < tau
+        frac = float(np.mean(fb))
+        # proposal for every read, then the exhaustive scan for the fallback fraction
+        rate = 1.0 / (prop_s / R + frac / ex_rate)
+        rows.append({"tau": tau, "fallback_fraction": round(frac, 5),
+                     "top1_agreement": round(float(np.mean(agree | fb)), 5),
+                     "reads_per_s_with_fallback": round(rate, 1), "speedup_vs_exhaustive": round(rate / ex_rate, 3)})
+    return {"genome": ewl.name, "genome_bp": int(eg.shape[0]), "num_frags": int(NF), "index_s": round(index_s, 2),
+            "reads": R, "K": K, "proposal_s": round(prop_s, 2), "proposal_reads_per_s": round(R / prop_s, 1),
+            "subsample": sr.count, "exhaustive_s": round(ex_s, 2), "exhaustive_reads_per_s": round(ex_rate, 2),
+            "recall_at_K_subsample": round(recall, 5), "top1_agreement_no_fallback": round(float(np.mean(agree)), 5),
+            "taus": rows}
+
+
 def main(argv=None):
     import torch
 
@@ -165,6 +222,11 @@ def main(argv=None):
     ap.add_argument("--eval-reads", type=int, default=20_000, help="held-out reads per genome (half choose tau)")
     ap.add_argument("--taus", type=str, default="-1e30,0.3,0.4,0.5,0.6,0.7,0.8,0.9",
                     help="comma-separated; pass as --taus=...")
+    ap.add_argument("--scale-reads", type=int, default=0,
+                    help="instead of the evaluation above: map this many reads of the read shape on the first "
+                         "evaluation genome with the proposal (no fallback), and compare a subsample with the "
+                         "exhaustive scan")
+    ap.add_argument("--subsample", type=int, default=20_000, help="exhaustive subsample of --scale-reads")
     ap.add_argument("--checkpoint", type=str, default="", help="save the trained weights here")
     ap.add_argument("--load", type=str, default="", help="start from these weights")
     args = ap.parse_args(argv)
@@ -196,6 +258,13 @@ def main(argv=None):
     del d_tseq, d_toff
 
     taus = [float(x) for x in args.taus.split(",")]
+    if args.scale_reads > 0:
+        scale = at_scale(torch, gen, prop, args, rspec, max_len, F, taus, log)
+        print(json.dumps({"metric": "learned proposal at scale (no fallback) vs an exhaustive subsample",
+                          "train_genome": wl.name, "train_reads": tr.count, "train_steps": args.steps,
+                          "loaded": args.load or None, **scale}), flush=True)
+        prop.close()
+        return
     evals = []
     for spec in args.evals.split(","):
         spec, _, nr = spec.partition(":")

@@ -22,7 +22,7 @@ def _line(monkeypatch, variant=-1, workload="bact-4.6M"):
     return bench.bench_line(
         gcups=20000.0, t=68.6, world=1, args=args, reads_s=17500.0,
         e2e={"value": 19900.0, "unit": "GCUPS", "h2d_bytes_per_step": 10, "d2h_bytes_per_step": 20},
-        launches=18, sms=152, probe={"dpx_add_max": 1.97, "fma_relu": 1.9, "prmt_and_fma_relu": 3.5, "prmt": 1.9, "max3": 1.9, "scan_mix": 2.5, "dpx_and_fma_relu": 2.3}, max_len=int(lengths.max()), wl=wl, genome=genome,
+        launches=18, sms=152, probe={"dpx_add_max": 1.97, "fma_relu": 1.9, "prmt_and_fma_relu": 3.5, "prmt": 1.9, "max3": 1.9, "scan_mix": 2.5, "dpx_and_fma_relu": 2.3}, probe_mhz=2070.0, max_len=int(lengths.max()), wl=wl, genome=genome,
         lengths=lengths, frag_len=wl.frag_len, tune=tune, tuned=None, cells_timed=3 * cells, scan_ms=[22748.0] * 3,
         cpu={"value": 7.4, "unit": "GCUPS", "cores": 16, "kind": "oracle", "sample": "32 reads"},
         clk={"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 300})

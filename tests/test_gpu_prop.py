@@ -2,8 +2,9 @@
 the exact path:
 
 * embeddings: BF16 tensor-core conv stack vs the fp64 oracle with the same rounding points
-  (tolerance from the BF16 activation rounding: 2e-2 absolute per coordinate of a unit vector);
-* parameter gradients vs the oracle's backward pass (relative error of the whole vector);
+  (bounded in BF16 ulps: at most 1% of the coordinates off by more than one ulp);
+* parameter gradients vs the oracle's backward pass (relative error of the whole vector and of
+  every parameter block, 1e-2 / 1.5e-2);
 * input codes (reads, both strands; genome windows) bit-exact;
 * proposal + exact rescoring: with K = all fragments, and with every read falling back, the
   result equals the exhaustive scan bit for bit; with small K the rescored best/second equal
@@ -73,8 +74,8 @@ def test_embeddings_match_oracle(mss):
     got = d_emb.cpu().numpy().reshape(-1, 128)
     for i, L in enumerate(lens):
         want, _ = po.forward(params.astype(np.float64), codes[i, :L])
-        assert np.abs(got[i] - want).max() < 2e-2, (i, L, np.abs(got[i] - want).max())
-        assert np.dot(got[i], want) > 0.999
+        assert np.abs(got[i] - want).max() < 3e-3, (i, L, np.abs(got[i] - want).max())
+        assert np.dot(got[i], want) > 0.99999
     prop.close()
 
 
@@ -89,8 +90,10 @@ def test_embedding_coordinates_within_one_bf16_ulp(mss):
     same places as the kernels, so a coordinate can differ only where an FP32 sum of the
     tensor cores (accumulated in another order than the oracle's exact sum) falls on the
     other side of a BF16 rounding boundary; such a flip moves an activation by one BF16 ulp.
-    Bound: no coordinate off by more than 4 BF16 ulps of its value, and at most 1% of the
-    coordinates off by more than one ulp."""
+    Where such a flip moves the pooling's argmax the coordinate can move by more (measured on
+    GB300: 0.35-0.49% of the coordinates above one ulp, 64-76% identical, at most 23 ulps,
+    absolute differences at most 1.2e-3).  Bound: at most 1% of the coordinates off by more
+    than one ulp, every coordinate within 2e-3, and the cosine to the oracle above 0.99999."""
     import torch
     prop = mss.Proposal(seed=6)
     params = random_params(41)
@@ -113,8 +116,10 @@ def test_embedding_coordinates_within_one_bf16_ulp(mss):
     over1 = float(np.mean(ulps[nz] > 1.0))
     stats = f"max {ulps[nz].max():.2f} ulp, {over1:.4%} of {nz.sum()} coordinates above 1 ulp, " \
             f"{float(np.mean(ulps[nz] <= 1e-3)):.2%} equal to 1e-3 ulp"
-    assert ulps[nz].max() <= 4.0, stats
     assert over1 <= 0.01, stats
+    assert diff.max() <= 2e-3, stats
+    cos = np.sum(got * want, axis=1) / (np.linalg.norm(got, axis=1) * np.linalg.norm(want, axis=1))
+    assert cos.min() > 0.99999, (cos.min(), stats)
     prop.close()
 
 
@@ -135,14 +140,16 @@ def test_gradients_match_oracle(mss):
     torch.cuda.synchronize()
     got = d_grad.cpu().numpy().astype(np.float64)
     want = sum(po.backward(params.astype(np.float64), codes[i, :L], demb[i]) for i, L in enumerate(lens))
+    # the same BF16 rounding points on both sides: only FP32 summation order differs (measured
+    # on GB300: 2.3e-3 relative over the whole vector, at most 3.7e-3 per parameter block)
     rel = np.linalg.norm(got - want) / np.linalg.norm(want)
-    assert rel < 5e-2, rel
+    assert rel < 1e-2, rel
     # every block, not just the total
     o = 0
     for size in [po.TAPS * 4 * po.C, po.C] + [po.TAPS * po.C * po.C, po.C] * 3:
         g, w_ = got[o:o + size], want[o:o + size]
         if np.linalg.norm(w_) > 1e-6:
-            assert np.linalg.norm(g - w_) / np.linalg.norm(w_) < 8e-2, (o, size)
+            assert np.linalg.norm(g - w_) / np.linalg.norm(w_) < 1.5e-2, (o, size)
         o += size
     prop.close()
 
@@ -176,7 +183,7 @@ def test_conv_many_items_per_cta(mss):
         assert np.array_equal(d_small.cpu().numpy().reshape(-1, 128), got[lo:hi]), lo
     for i in [0, 1, 2, 3] + list(rng.choice(n, size=8, replace=False)):
         want, _ = po.forward(params.astype(np.float64), codes[i, :lens[i]])
-        assert np.abs(got[i] - want).max() < 2e-2, (i, lens[i])
+        assert np.abs(got[i] - want).max() < 3e-3, (i, lens[i])
     m = 160
     demb = rng.normal(size=(m, 128)).astype(np.float32)
     d_grad = torch.zeros(po.param_count(), dtype=torch.float32, device="cuda")
@@ -184,7 +191,7 @@ def test_conv_many_items_per_cta(mss):
     torch.cuda.synchronize()
     g = d_grad.cpu().numpy().astype(np.float64)
     want = sum(po.backward(params.astype(np.float64), codes[i, :lens[i]], demb[i]) for i in range(m))
-    assert np.linalg.norm(g - want) / np.linalg.norm(want) < 5e-2
+    assert np.linalg.norm(g - want) / np.linalg.norm(want) < 1e-2
     prop.close()
 
 
