@@ -37,6 +37,10 @@ cudaError_t prop_conv_tc(const __nv_bfloat16* in, const void* wcanon, const floa
                          cudaStream_t s);
 cudaError_t prop_conv_wgrad(const __nv_bfloat16* in, const __nv_bfloat16* g, const int32_t* lens, float* dw, int32_t n,
                             int32_t rows, cudaStream_t s);
+// The same weight gradient on the fifth-generation tensor cores (wgrad_tc.cu); err: device
+// error word (a bounded wait that gives up sets ERR_TIMEOUT).
+cudaError_t prop_conv_wgrad_tc(const __nv_bfloat16* in, const __nv_bfloat16* g, const int32_t* lens, float* dw,
+                               int32_t n, int32_t rows, int32_t* err, cudaStream_t s);
 cudaError_t prop_bias_grad(const __nv_bfloat16* g, const int32_t* lens, float* db, int32_t n, int32_t rows,
                            cudaStream_t s);
 cudaError_t prop_l1_wgrad(const uint8_t* codes, const int32_t* lens, int32_t ld, const __nv_bfloat16* g, float* dw1,

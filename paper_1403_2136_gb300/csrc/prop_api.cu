@@ -142,7 +142,9 @@ mss_status backward(mss_prop* p, const uint8_t* codes, const int32_t* lens, int3
   p->launches += 1;
   for (int l = 4; l >= 2; --l) {
     // gcur = gradient of layer l's pre-activation; input activation of layer l is act[l - 2]
-    PCK(prop_conv_wgrad(a.act[l - 2].as<__nv_bfloat16>(), gcur, lens, gw + prop_off_w(l), n, rows, s), "wgrad");
+    PCK(prop_conv_wgrad_tc(a.act[l - 2].as<__nv_bfloat16>(), gcur, lens, gw + prop_off_w(l), n, rows,
+                           p->err.as<int32_t>(), s),
+        "wgrad");
     PCK(prop_bias_grad(gcur, lens, gw + prop_off_b(l), n, rows, s), "bias grad");
     PCK(prop_conv_tc(gcur, p->wfct[l - 2].p, nullptr, a.act[l - 2].as<__nv_bfloat16>(), lens, gnext, n, rows, 1,
                      p->err.as<int32_t>(), s),

@@ -314,6 +314,32 @@ def test_bounded_wait_gives_up_and_reports_timeout(mss):
     g.close()
 
 
+def test_map_sharded_over_nccl_one_rank(mss):
+    """shard.map_sharded through a one-rank NCCL process group on this GPU: the library's scan
+    of the rank's slice, the all-gather of the records on the device, the merge; equal to the
+    oracle on the whole genome (every box here has one GPU, so this is the NCCL path's only
+    run on hardware; the multi-rank exchange runs with gloo ranks on the CPU)."""
+    import socket
+    import torch
+    import torch.distributed as dist
+    from paper_1403_2136_gb300 import shard
+    wl = gen.scaled(gen.workloads()["bact-4.6M"], genome_len=120_000, reads=24)
+    genome, reads = gen.materialize(wl)
+    ml = int(np.diff(reads.offsets).max())
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    torch.cuda.set_device(0)
+    dist.init_process_group("nccl", init_method=f"tcp://127.0.0.1:{port}", rank=0, world_size=1)
+    try:
+        got = shard.map_sharded(genome, 2048, reads.seq, reads.offsets, 5, -4, ml)
+    finally:
+        dist.destroy_process_group()
+    want, _, _ = oracle.map_batch(genome, 2048, reads.seq, reads.offsets, 5, -4)
+    assert_hits_equal(got, want, "map_sharded over NCCL, one rank")
+
+
 # ---------------------------------------------------------------- MaxSSmap_fast (read step 2)
 @pytest.mark.parametrize("variant", [0, 1])
 def test_fast_step_tiny_50k(mss, variant):
