@@ -6,11 +6,9 @@
 // -> max over positions -> L2 normalisation.  Weights BF16, accumulation FP32.
 //
 // Kernels here (the 128 -> 128 conv itself, forward and backward-data, runs on the
-// fifth-generation tensor cores in conv_tc.cu; the read x fragment score GEMM with its fused
-// top K in score_tc.cu):
+// fifth-generation tensor cores in conv_tc.cu, its weight gradient in wgrad_tc.cu, the read x
+// fragment score GEMM with its fused top K in score_tc.cu):
 //   k_embed_l1      first layer (4 -> 128) as a gather-sum of per-base weight rows
-//   k_conv_wgrad    weight gradient, a GEMM over positions per tap on the BF16 mma.sync path
-//                   (fp32 atomics across CTAs)
 //   k_pool_norm     max over positions (first argmax kept), L2 norm
 //   k_pool_norm_bwd gradient of the norm routed to the argmax positions
 //   k_l1_wgrad      first-layer weight/bias gradients; k_bias_grad: bias gradients
@@ -28,36 +26,6 @@
 #include "tc.cuh"
 
 namespace mss {
-
-// ------------------------------------------------------------------------------------------
-// shared-memory tiles of 128 bf16 per row, 16-byte chunks XOR-swizzled by the row's low bits
-// so that 8 consecutive rows read by ldmatrix hit 8 different bank groups
-__device__ __forceinline__ uint32_t swz(int row, int chunk) { return (uint32_t)(row * 256 + ((chunk ^ (row & 7)) << 4)); }
-
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-
-__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
-               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-               : "r"(addr));
-}
-__device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
-               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-               : "r"(addr));
-}
-__device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
 
 // ------------------------------------------------------------------------------------------
 // layer 1: out[n][p][co] = relu(b[co] + sum_t w1[t][x[p+t-3]][co]) for p < len, else 0
@@ -124,98 +92,6 @@ __global__ void k_zero_halo(__nv_bfloat16* b0, __nv_bfloat16* b1, __nv_bfloat16*
 }
 
 // ------------------------------------------------------------------------------------------
-// shared-memory tiles of the weight-gradient GEMM (mma.sync): 134-row input tile + two 128-row
-// buffers of 256 bytes per row
-constexpr int kConvM = 128;
-constexpr int kConvThreads = 256;
-constexpr int kConvARows = kConvM + 6;
-constexpr size_t kConvSmem = (size_t)kConvARows * 256 + 2 * 128 * 256;
-
-// ------------------------------------------------------------------------------------------
-// weight gradient of a 128 -> 128 layer for one tap t: dw[t][ci][co] += sum_{n, p} in[n][p + t - 3][ci]
-// * g[n][p][co].  The (sequence, 128-position tile) pairs are split into contiguous runs, one
-// run per CTA; a CTA accumulates its run in registers and adds it to dw once (fp32 atomics).
-__global__ void __launch_bounds__(kConvThreads, 2)
-    k_conv_wgrad(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ g,
-                 const int32_t* __restrict__ lens, float* __restrict__ dw, int32_t n_seq, int32_t rows,
-                 int32_t tiles_per_cta) {
-  extern __shared__ __align__(128) uint8_t sm[];
-  const uint32_t sA = smem_u32(sm);          // in rows (positions p0 - 3 ...), 134 rows
-  const uint32_t sB = sA + kConvARows * 256;  // g rows of positions p0 .. p0 + 127
-  const int t = blockIdx.y;
-  const int tiles_per_seq = (rows - 6) / kConvM;
-  const int64_t total = (int64_t)n_seq * tiles_per_seq;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int wm = warp & 3, wn = warp >> 2;  // warp tile: ci wm*32 + [0,32), co wn*64 + [0,64)
-  float acc[2][8][4];
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 8; ++j)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
-  bool any = false;
-  for (int64_t tile = (int64_t)blockIdx.x * tiles_per_cta;
-       tile < total && tile < (int64_t)(blockIdx.x + 1) * tiles_per_cta; ++tile) {
-    const int n = (int)(tile / tiles_per_seq);
-    const int p0 = (int)(tile - (int64_t)n * tiles_per_seq) * kConvM;
-    if (p0 >= lens[n]) continue;  // uniform across the CTA
-    any = true;
-    __syncthreads();  // the previous tile's shared data is no longer read
-    const __nv_bfloat16* inb = in + ((int64_t)n * rows + p0) * kPropC;
-    for (int e = tid; e < kConvARows * 16; e += kConvThreads) {
-      const int r = e >> 4, c = e & 15;
-      cp_async16(sA + swz(r, c), inb + r * kPropC + c * 8);
-    }
-    const __nv_bfloat16* gb = g + ((int64_t)n * rows + p0 + 3) * kPropC;
-    for (int e = tid; e < 128 * 16; e += kConvThreads) {
-      const int r = e >> 4, c = e & 15;
-      cp_async16(sB + swz(r, c), gb + r * kPropC + c * 8);
-    }
-    cp_async_commit();
-    cp_async_wait_all();
-    __syncthreads();
-#pragma unroll 2
-    for (int kk = 0; kk < 8; ++kk) {  // 16 positions per step
-      uint32_t af[2][4];
-#pragma unroll
-      for (int mi = 0; mi < 2; ++mi) {
-        // A[m = ci][k = p] = in[p + t - 3][ci]: transposed load of the [p][ci] tile
-        const int i = lane >> 3;
-        const int r = kk * 16 + (i >> 1) * 8 + (lane & 7) + t;
-        const int ch = (wm * 32 + mi * 16) / 8 + (i & 1);
-        ldsm_x4_t(sA + swz(r, ch), af[mi][0], af[mi][1], af[mi][2], af[mi][3]);
-      }
-#pragma unroll
-      for (int nj = 0; nj < 8; nj += 2) {
-        const int i = lane >> 3;
-        const int r = kk * 16 + (i & 1) * 8 + (lane & 7);
-        const int ch = (wn * 64 + nj * 8) / 8 + (i >> 1);
-        uint32_t b0, b1, b2, b3;
-        ldsm_x4_t(sB + swz(r, ch), b0, b1, b2, b3);
-#pragma unroll
-        for (int mi = 0; mi < 2; ++mi) {
-          mma_bf16(acc[mi][nj], af[mi], b0, b1);
-          mma_bf16(acc[mi][nj + 1], af[mi], b2, b3);
-        }
-      }
-    }
-  }
-  if (!any) return;
-  float* dwt = dw + (int64_t)t * kPropC * kPropC;
-#pragma unroll
-  for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-    for (int nj = 0; nj < 8; ++nj)
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int ci = wm * 32 + mi * 16 + (lane >> 2) + h * 8;
-        const int co = wn * 64 + nj * 8 + (lane & 3) * 2;
-        atomicAdd(dwt + ci * kPropC + co, acc[mi][nj][h * 2]);
-        atomicAdd(dwt + ci * kPropC + co + 1, acc[mi][nj][h * 2 + 1]);
-      }
-}
-
 // bias gradient: db[co] += sum_{n, p < len} g[n][p + 3][co]
 __global__ void k_bias_grad(const __nv_bfloat16* __restrict__ g, const int32_t* __restrict__ lens, float* db,
                             int32_t rows) {
@@ -575,22 +451,6 @@ cudaError_t prop_zero_halo(__nv_bfloat16* b0, __nv_bfloat16* b1, __nv_bfloat16* 
   return cudaGetLastError();
 }
 
-
-cudaError_t prop_conv_wgrad(const __nv_bfloat16* in, const __nv_bfloat16* g, const int32_t* lens, float* dw, int32_t n,
-                            int32_t rows, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_conv_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kConvSmem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  const int64_t total = (int64_t)n * ((rows - 6) / kConvM);
-  const int64_t ctas = total < 64 ? total : 64;  // runs of tiles per tap
-  const int32_t per = (int32_t)((total + ctas - 1) / ctas);
-  dim3 grid((unsigned)((total + per - 1) / per), (unsigned)kPropTaps);
-  k_conv_wgrad<<<grid, kConvThreads, kConvSmem, s>>>(in, g, lens, dw, n, rows, per);
-  return cudaGetLastError();
-}
 
 cudaError_t prop_bias_grad(const __nv_bfloat16* g, const int32_t* lens, float* db, int32_t n, int32_t rows,
                            cudaStream_t s) {

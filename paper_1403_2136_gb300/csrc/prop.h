@@ -35,10 +35,9 @@ cudaError_t prop_canon_weights(const __nv_bfloat16* w, void* dst, cudaStream_t s
 cudaError_t prop_conv_tc(const __nv_bfloat16* in, const void* wcanon, const float* bias, const __nv_bfloat16* prev,
                          const int32_t* lens, __nv_bfloat16* out, int32_t n, int32_t rows, int mode, int32_t* err,
                          cudaStream_t s);
-cudaError_t prop_conv_wgrad(const __nv_bfloat16* in, const __nv_bfloat16* g, const int32_t* lens, float* dw, int32_t n,
-                            int32_t rows, cudaStream_t s);
-// The same weight gradient on the fifth-generation tensor cores (wgrad_tc.cu); err: device
-// error word (a bounded wait that gives up sets ERR_TIMEOUT).
+// Weight gradient of a 128 -> 128 layer, dw[t][ci][co] += sum over sequences and positions p
+// of in[p + t - 3][ci] * g[p][co], on the fifth-generation tensor cores (wgrad_tc.cu); err:
+// device error word (a bounded wait that gives up sets ERR_TIMEOUT).
 cudaError_t prop_conv_wgrad_tc(const __nv_bfloat16* in, const __nv_bfloat16* g, const int32_t* lens, float* dw,
                                int32_t n, int32_t rows, int32_t* err, cudaStream_t s);
 cudaError_t prop_bias_grad(const __nv_bfloat16* g, const int32_t* lens, float* db, int32_t n, int32_t rows,

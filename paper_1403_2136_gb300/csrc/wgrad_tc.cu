@@ -43,7 +43,9 @@ constexpr uint32_t kWgSmem = 2 * kWgStage + 64;           // two stages, mbarrie
 constexpr uint64_t kWgWaitNs = 2000000000ull;
 // MN-major operands without swizzling: core matrices of 8 rows (K) x 16 bytes (8 MN
 // elements); the descriptor's leading offset is the distance between core matrices adjacent
-// in MN, its stride offset the distance between core matrices adjacent in K (8 rows = 128 B).
+// in K (8 rows = 128 B here), its stride offset the distance between core matrices adjacent in
+// MN (checked on GB300 with a single MMA of known integers against both assignments, and with a
+// start address inside a core matrix, which the tap shift uses).
 constexpr uint32_t kWgCoreK = 128;
 // instruction descriptor: BF16 x BF16 -> FP32, M = N = 128, A and B MN-major (bits 15, 16)
 constexpr uint32_t kWgIdesc = idesc_bf16_f32(128, 128) | (1u << 15) | (1u << 16);
@@ -121,8 +123,8 @@ __global__ void __launch_bounds__(kWgThreads, 1)
       for (int j = 0; j < ntaps; ++j) {
 #pragma unroll
         for (int kk = 0; kk < kWgTile / 16; ++kk)
-          tc_mma_bf16(tmem + (uint32_t)(j * 128), smem_desc(a0 + (uint32_t)(j + 16 * kk) * 16, kWgAStride, kWgCoreK),
-                      smem_desc(b0 + (uint32_t)(16 * kk) * 16, kWgBStride, kWgCoreK), kWgIdesc,
+          tc_mma_bf16(tmem + (uint32_t)(j * 128), smem_desc(a0 + (uint32_t)(j + 16 * kk) * 16, kWgCoreK, kWgAStride),
+                      smem_desc(b0 + (uint32_t)(16 * kk) * 16, kWgCoreK, kWgBStride), kWgIdesc,
                       (issued > 0 || kk > 0) ? 1u : 0u);
       }
       tc_commit(&done[s]);
