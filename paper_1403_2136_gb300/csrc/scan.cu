@@ -259,12 +259,26 @@ __global__ void __launch_bounds__(NT, MINB) k_scan(ScanArgs a) {
         for (int col = tid; col < ncols; col += NT) {
           const int P = col * SPAN;
           const uint64_t gw = ((((uint64_t)rg2[(P >> 4) + 1]) << 32) | rg2[P >> 4]) >> (2 * (P & 15));
-          const uint64_t vw = ((((uint64_t)rgm[(P >> 5) + 1]) << 32) | rgm[P >> 5]) >> (P & 31);
+          const uint32_t vw = (uint32_t)(((((uint64_t)rgm[(P >> 5) + 1]) << 32) | rgm[P >> 5]) >> (P & 31));
+          // one byte per position, n = the 2-bit code, or the N code where the valid bit is 0
+          // (packed N and padding carry code 0), four positions per word, built with
+          // carry-free multiplies: bytes of 4 codes -> 2-bit fields 8 bits apart; 4 valid
+          // bits -> bit 0 of 4 bytes
+          uint32_t nb[3 * D / 4];
+#pragma unroll
+          for (int k = 0; k < 3 * D / 4; ++k) {
+            const uint32_t b = prmt(k < 4 ? (uint32_t)gw : (uint32_t)(gw >> 32), 0u, 0x4440u | (uint32_t)(k & 3));
+            const uint32_t codes = ((((b * 4097u) & 0x000F000Fu) * 65u) & 0x03030303u);
+            const uint32_t vs = ((((vw >> (4 * k)) & 0xFu) * 0x00204081u) & 0x01010101u);
+            nb[k] = codes + (F16 ? 5u : 4u) * (0x01010101u - vs);
+          }
 #pragma unroll
           for (int r = 0; r < SPAN; ++r) {
-            const uint32_t c1 = ((vw >> r) & 1u) ? (uint32_t)((gw >> (2 * r)) & 3u) : 4u;
-            const uint32_t c2 = ((vw >> (r + D)) & 1u) ? (uint32_t)((gw >> (2 * (r + D))) & 3u) : 4u;
-            sel[r * W + col] = make_sel<F16>(c1, c2);
+            // bytes [n(P + r), n(P + r + D), 0, 0] (the zero bytes replicate the sign of a byte
+            // <= 5), then the selector word of make_sel with one multiply-add
+            const uint32_t t2 =
+                prmt(nb[r >> 2], nb[(r + D) >> 2], (uint32_t)(r & 3) | ((uint32_t)(4 + (r & 3)) << 4) | 0x8800u);
+            sel[r * W + col] = F16 ? t2 * 16u + 0x0404u : t2 * 17u + 0x8080u;
           }
         }
       }
