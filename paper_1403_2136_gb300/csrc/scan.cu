@@ -398,20 +398,31 @@ __global__ void __launch_bounds__(NT, MINB) k_scan(ScanArgs a) {
         const uint32_t hi = (ds + D + j < bnd) ? 0xFFFF0000u : 0u;
         maskA[j] = split ? (lo | hi) : 0xFFFFFFFFu;
       }
+      // the maxima are non-negative, so their 16-bit patterns (f16 or int16) order like their
+      // values: reduce the patterns, decode once
 #pragma unroll
       for (int r = 0; r < RG; ++r) {
         uint32_t xa = 0u, xb = 0u;
+        if (!split) {
 #pragma unroll
-        for (int j = 0; j < D; ++j) {
-          xa = __vimax3_s16x2(xa, M[2 * r][j] & maskA[j], M[2 * r + 1][j] & maskA[j]);
-          xb = __vimax3_s16x2(xb, M[2 * r][j] & ~maskA[j], M[2 * r + 1][j] & ~maskA[j]);
-        }
-        const int32_t vA = max(lane_value<F16>(xa), lane_value<F16>(xa >> 16));
-        const int32_t vB = max(lane_value<F16>(xb), lane_value<F16>(xb >> 16));
-        if (uni) {
-          const int32_t v = __reduce_max_sync(0xffffffffu, vA);
-          if (lane == 0 && v > 0) atomicMax(&ring[r * S + (int)(fA0 % S)], v);
+          for (int j = 0; j < D; ++j) xa = __vimax3_s16x2(xa, M[2 * r][j], M[2 * r + 1][j]);
         } else {
+#pragma unroll
+          for (int j = 0; j < D; ++j) {
+            xa = __vimax3_s16x2(xa, M[2 * r][j] & maskA[j], M[2 * r + 1][j] & maskA[j]);
+            xb = __vimax3_s16x2(xb, M[2 * r][j] & ~maskA[j], M[2 * r + 1][j] & ~maskA[j]);
+          }
+        }
+        const uint32_t pa = max(xa & 0xFFFFu, xa >> 16);
+        if (uni) {
+          const uint32_t pm = __reduce_max_sync(0xffffffffu, pa);
+          if (lane == 0) {
+            const int32_t v = lane_value<F16>(pm);
+            if (v > 0) atomicMax(&ring[r * S + (int)(fA0 % S)], v);
+          }
+        } else {
+          const int32_t vA = lane_value<F16>(pa);
+          const int32_t vB = lane_value<F16>(max(xb & 0xFFFFu, xb >> 16));
           if (vA > 0) atomicMax(&ring[r * S + (int)(fA % S)], vA);
           if (vB > 0) atomicMax(&ring[r * S + (int)((fA + 1) % S)], vB);
         }
