@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--autotune", action="store_true",
                     help="pick the scan shape and fragment length with mss_autotune on a read sample first")
     ap.add_argument("--autotune-reads", type=int, default=256)
+    ap.add_argument("--threads", type=int, default=0, choices=[0, 128, 256],
+                    help="scan threads per CTA (0: the library's default)")
     ap.add_argument("--read-step", type=int, default=1, choices=[1, 2],
                     help="2: MaxSSmap_fast (every other read base in phase one)")
     ap.add_argument("--no-proposal", action="store_true", help="skip the learned-proposal measurement")
@@ -377,7 +379,8 @@ def bench_line(*, gcups, t, world, args, reads_s, e2e, launches, sms, probe, max
     mix = mix_ceiling_tcups(probe, sms, clk_mhz)
     lanes = scan_lanes(max_len, wl.match, wl.mismatch, tune["variant"])
     default_run = (wl.name == gen.workloads()[args.workload].name and args.workload == "bact-4.6M"
-                   and args.read_step == 1 and not args.autotune and frag_len == 2048 and args.batch == 50_000)
+                   and args.read_step == 1 and not args.autotune and frag_len == 2048 and args.batch == 50_000
+                   and args.threads == 0)
     traffic = SCAN_DRAM_BYTES_DEFAULT if default_run else None
     scan_mean_ms = statistics.mean(scan_ms)
     achieved = cells_timed / (sum(scan_ms) * 1e-3) / 1e12
@@ -450,6 +453,8 @@ def main():
     g = mss.mss_load_genome(genome, frag_len=wl.frag_len, max_read_len=max_len)
     info = g.info()
     mss.mss_set_read_step(g, args.read_step)
+    if args.threads:
+        mss.mss_set_tune(g, threads=args.threads)
     mss.mss_scan_timing(g, True)
     stream = torch.cuda.Stream(device=dev)
     d_parts = [(torch.from_numpy(s).to(dev), torch.from_numpy(o).to(dev), int(o.shape[0] - 1)) for s, o in parts]

@@ -123,7 +123,8 @@ typedef struct {
   int32_t ctas_per_sm;   /* persistent CTAs per SM (0 = occupancy maximum) */
   int32_t min_items_per_cta; /* split the genome into chunks until there are this many work
                                 items per CTA (0 = default 4) */
-  int32_t reserved;      /* must be 0 */
+  int32_t threads;       /* threads per CTA: 256 or 128 (0 = default 256); 128 is built for 8
+                            pairs x 4 queries at read step 1 without base qualities */
 } mss_tune;
 
 /* Load and 2-bit pack a genome (host ASCII, length len >= 1).  Creates *out. */

@@ -70,7 +70,7 @@ class GenomeInfo(ctypes.Structure):
 
 class Tune(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int32), ("pairs", ctypes.c_int32), ("queries", ctypes.c_int32),
-                ("ctas_per_sm", ctypes.c_int32), ("min_items_per_cta", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("ctas_per_sm", ctypes.c_int32), ("min_items_per_cta", ctypes.c_int32), ("threads", ctypes.c_int32)]
 
 
 _lib = None
@@ -229,8 +229,8 @@ def mss_get_read_step(g: Genome) -> int:
     return int(load_library().mss_get_read_step(g.handle))
 
 
-def mss_set_tune(g: Genome, variant=-1, pairs=0, queries=0, ctas_per_sm=0, min_items_per_cta=0):
-    t = Tune(variant, pairs, queries, ctas_per_sm, min_items_per_cta, 0)
+def mss_set_tune(g: Genome, variant=-1, pairs=0, queries=0, ctas_per_sm=0, min_items_per_cta=0, threads=0):
+    t = Tune(variant, pairs, queries, ctas_per_sm, min_items_per_cta, threads)
     _check(load_library().mss_set_tune(g.handle, ctypes.byref(t)), "mss_set_tune")
 
 

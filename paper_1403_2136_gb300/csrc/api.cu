@@ -193,7 +193,7 @@ mss_status resolve_config(const mss_ctx* c, int32_t max_len, const mss_score_par
   cfg->variant = variant;
   cfg->pairs = t.pairs ? t.pairs : 8;
   cfg->queries = t.queries ? t.queries : (cfg->pairs == 8 ? 4 : 8);
-  cfg->threads = 256;
+  cfg->threads = t.threads ? t.threads : 256;
   cfg->max_len = max_len;
   cfg->step = c->read_step;
   cfg->pssm = pssm;
@@ -201,6 +201,8 @@ mss_status resolve_config(const mss_ctx* c, int32_t max_len, const mss_score_par
     return fail(MSS_EINVAL, "read step 2 is built for 8 lane pairs x 4 query strands only");
   if (pssm && (cfg->pairs != 8 || cfg->queries != 4 || cfg->step != 1))
     return fail(MSS_EINVAL, "base qualities are built for read step 1 and 8 lane pairs x 4 query strands only");
+  if (cfg->threads == 128 && (cfg->pairs != 8 || cfg->queries != 4 || cfg->step != 1 || pssm))
+    return fail(MSS_EINVAL, "128 threads per CTA are built for 8 lane pairs x 4 query strands at read step 1 only");
   *slots = scan_ring_slots(*cfg, c->F);
   *smem = scan_smem_bytes(*cfg, max_len, *slots);
   if (*smem == 0)
@@ -580,7 +582,7 @@ mss_status mss_set_tune(mss_ctx* c, const mss_tune* t) {
   if (t->variant < -1 || t->variant > 1) return fail(MSS_EINVAL, "variant must be -1, 0 or 1");
   if (t->pairs != 0 && t->pairs != 4 && t->pairs != 8) return fail(MSS_EINVAL, "pairs must be 4 or 8");
   if (t->queries != 0 && t->queries != 4 && t->queries != 8) return fail(MSS_EINVAL, "queries must be 4 or 8");
-  if (t->reserved != 0) return fail(MSS_EINVAL, "mss_tune.reserved must be 0");
+  if (t->threads != 0 && t->threads != 128 && t->threads != 256) return fail(MSS_EINVAL, "threads must be 128 or 256");
   if ((t->pairs == 8 ? 8 : 4) == 8 && t->queries == 8) return fail(MSS_EINVAL, "pairs 8 with queries 8 is not built");
   if (t->pairs == 8 && t->queries == 0) {
     mss_tune u = *t;
@@ -764,6 +766,10 @@ mss_status mss_autotune(mss_ctx* c, const char* d_reads, const int64_t* d_offset
         const int pairs = pq == 1 ? 8 : 4, queries = pq == 1 ? 4 : (pq == 2 ? 4 : 8);
         mss_tune t{v, pairs, queries, cps, 0, 0};
         cands.push_back(t);
+        if (pq == 1 && c->read_step == 1 && !c->call_quals) {  // the 128-thread shape
+          t.threads = 128;
+          cands.push_back(t);
+        }
       }
   std::vector<int64_t> frags = {c->F};
   if (allow_frag_len) frags = {1024, 2048, 4096, 8192};

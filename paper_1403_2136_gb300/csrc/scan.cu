@@ -471,7 +471,11 @@ __global__ void __launch_bounds__(NT, MINB) k_scan(ScanArgs a) {
   X(false, 8, 4, 256, 2432, 2, 2, false)   \
   X(true, 8, 4, 256, 2432, 2, 2, false)    \
   X(false, 8, 4, 256, 512, 2, 1, true)     \
-  X(false, 8, 4, 256, 2432, 2, 1, true)
+  X(false, 8, 4, 256, 2432, 2, 1, true)    \
+  X(false, 8, 4, 128, 512, 4, 1, false)    \
+  X(true, 8, 4, 128, 512, 4, 1, false)     \
+  X(false, 8, 4, 128, 2432, 4, 1, false)   \
+  X(true, 8, 4, 128, 2432, 4, 1, false)
 
 // reads up to 512 bases use selector rows sized for 512 (less shared memory per CTA)
 static int maxl_of(int32_t max_len) { return max_len <= 512 ? 512 : 2432; }

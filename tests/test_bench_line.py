@@ -18,7 +18,7 @@ def _line(monkeypatch, variant=-1, workload="bact-4.6M"):
     genome = np.zeros(4_600_000, dtype=np.uint8)
     lengths = np.array([100] * 4 + [150] * 4, dtype=np.int64)
     cells = bench.cells_of(lengths, genome.shape[0], wl.frag_len)
-    tune = {"variant": variant, "pairs": 0, "queries": 0, "ctas_per_sm": 0, "min_items_per_cta": 0, "reserved": 0}
+    tune = {"variant": variant, "pairs": 0, "queries": 0, "ctas_per_sm": 0, "min_items_per_cta": 0, "threads": 0}
     return bench.bench_line(
         gcups=20000.0, t=68.6, world=1, args=args, reads_s=17500.0,
         e2e={"value": 19900.0, "unit": "GCUPS", "h2d_bytes_per_step": 10, "d2h_bytes_per_step": 20},

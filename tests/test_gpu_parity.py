@@ -74,6 +74,26 @@ def test_scan_configurations(mss, pairs, queries, variant):
     assert_hits_equal(hits, oh, f"config v{variant} D{pairs} Q{queries}")
 
 
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("max_len", [250, 2432])
+def test_scan_with_128_threads_per_cta(mss, variant, max_len):
+    """The 128-thread CTA shape (tiles of 2,048 diagonals, four CTAs per SM) on a ragged mix of
+    read lengths, bit-exact against the oracle; the shapes it is not built for are rejected."""
+    wl = gen.scaled(gen.workloads()["chrom-230M"], genome_len=70_000, reads=30)
+    genome, reads = gen.materialize(wl)
+    hits, _, _, oh, _, _ = run_both(mss, genome, reads.seq, reads.offsets, 1000, 5, -4, max_len=max_len,
+                                    tune={"variant": variant, "pairs": 8, "queries": 4, "threads": 128},
+                                    procs=cpu_count())
+    assert_hits_equal(hits, oh, f"128 threads v{variant} max_len {max_len}")
+    g = mss.mss_load_genome(genome, frag_len=1000, max_read_len=250)
+    with pytest.raises(mss.MssError):
+        mss.mss_set_tune(g, threads=64)
+    mss.mss_set_tune(g, pairs=4, queries=8, threads=128)
+    with pytest.raises(mss.MssError):
+        mss.mss_map_reads(g, reads.seq, reads.offsets, 5, -4)
+    g.close()
+
+
 @pytest.mark.parametrize("items", [1, 4, 64])
 def test_chunking_is_result_neutral(mss, items):
     """One chunk per group, a few, or many chunks per group must give the same top-2 (the
