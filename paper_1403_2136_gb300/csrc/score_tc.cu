@@ -171,7 +171,22 @@ __device__ void warp_emit(const uint32_t* key, const int32_t* frag, int n, int K
   }
 }
 
-__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"n"(kTcEpiWarps * 32) : "memory"); }
+// The four epilogue warps of a read group (warps 4g .. 4g + 3 append to reads 16g .. 16g + 15
+// and compact them) synchronise on their own named barrier 2 + g; the "or" form also makes
+// every warp of the group take the same abort decision.
+__device__ __forceinline__ void grp_bar(int g) { asm volatile("bar.sync %0, 128;" ::"r"(2 + g) : "memory"); }
+__device__ __forceinline__ bool grp_bar_or(int g, bool p) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred pi, po;\n\t"
+      "setp.ne.u32 pi, %1, 0;\n\t"
+      "bar.red.or.pred po, %2, 128, pi;\n\t"
+      "selp.u32 %0, 1, 0, po;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)p), "r"(2 + g)
+      : "memory");
+  return r != 0;
+}
 
 __global__ void __launch_bounds__(kTcThreads, 1) k_score_topk(TcArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -270,7 +285,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_topk(TcArgs a) {
   } else {
     // ---- epilogue: warp w reads accumulator lanes 32 (w mod 4) .. + 31 (fragments) and
     //      columns 32 (w div 4) .. + 31 (16 reads): strand maximum, threshold, candidate buffers
-    const int q = warp & 3, rbase = 16 * (warp >> 2);
+    const int q = warp & 3, grp = warp >> 2, rbase = 16 * grp;
     const int frow = 32 * q + lane;  // fragment row of this thread in a tile
     for (int j = 0; j < nt; ++j) {
       const int s = j & 1;
@@ -325,20 +340,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_topk(TcArgs a) {
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&tmem_free[s]);
-      epi_bar();  // every append of this tile is done
-      const bool abort = *s_abort != 0;
+      // every append of the group's reads for this tile is done
+      const bool abort = grp_bar_or(grp, *s_abort != 0);
       if (!abort)
-        for (int r = warp; r < kTcReads; r += kTcEpiWarps)
+        for (int r = rbase + q; r < rbase + 16; r += 4)
           if (s_cnt[r] > kTcCap - kTcM) {
             s_theta[r] = warp_select(s_key + r * kTcCap, s_frag + r * kTcCap, s_cnt[r], a.K, lane);
             if (lane == 0) s_cnt[r] = a.K;
             __syncwarp();
           }
-      epi_bar();  // buffers compacted before the next tile's appends
+      grp_bar(grp);  // the group's buffers compacted before its next appends
       if (abort) break;
     }
-    // the K best of every read
-    for (int r = warp; r < kTcReads; r += kTcEpiWarps) {
+    // the K best of every read of the group (its buffers are final after the last group barrier)
+    for (int r = rbase + q; r < rbase + 16; r += 4) {
       const int rg = r0 + r;
       if (rg >= a.R) continue;
       int n = s_cnt[r];
