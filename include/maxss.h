@@ -266,7 +266,7 @@ MSS_API mss_status mss_check_wait_timeout(mss_ctx* ctx, uint32_t limit_us, void*
 
 /* ==========================================================================================
  * Learned fragment proposal (a step added to the method; the paper has none).  A small 1-D
- * CNN (one-hot bases -> 4 x conv1d(128 channels, kernel 7, "same", ReLU) -> max over
+ * CNN (one-hot bases -> 4 x conv1d(128 channels, kernel 7, "same", ReLU) -> max (or mean) over
  * positions -> L2 norm; BF16 weights, FP32 accumulation) embeds reads and genome fragments.
  * The dot product ranks fragments per read (maximum over the read's two strands); the exact
  * scan then runs only on the top K fragments, and reads whose best proposal score is below a
@@ -285,6 +285,17 @@ MSS_API void mss_prop_free(mss_prop* p);
 MSS_API int64_t mss_prop_param_count(void);
 MSS_API mss_status mss_prop_get_params(const mss_prop* p, float* host, int64_t n);
 MSS_API mss_status mss_prop_set_params(mss_prop* p, const float* host, int64_t n);
+/* Pooling of the last layer's outputs over a sequence's positions (a reading the proposal
+   leaves open): MSS_POOL_MAX (the default) keeps each channel's maximum (the first position
+   on ties) and routes its gradient there; MSS_POOL_MEAN takes each channel's mean over the
+   sequence's positions (FP32 sum / length) and spreads the gradient with weight 1 / length.
+   The setting applies to every later embedding, gradient and training step and is saved in
+   checkpoints; an index built under another pooling (or other weights) must be rebuilt.
+   MSS_EINVAL for another value.  mss_prop_get_pooling returns -1 for a null model. */
+#define MSS_POOL_MAX 0
+#define MSS_POOL_MEAN 1
+MSS_API mss_status mss_prop_set_pooling(mss_prop* p, int32_t pooling);
+MSS_API int32_t mss_prop_get_pooling(const mss_prop* p);
 /* Input codes for the network (device buffers, codes 0..3 = ACGT, 4 = N/padding, row stride
    ld): reads (d_idx selects reads, d_strand 1 = reverse complement; both may be NULL) and
    genome windows [start, start + len). */
@@ -325,7 +336,8 @@ MSS_API mss_status mss_map_reads_proposed(mss_ctx* ctx, mss_prop* p, const char*
                                           int32_t R, int32_t max_len, const mss_score_params* sp, int32_t K,
                                           float tau, mss_hit* d_out, int32_t* d_cand, float* d_top_score,
                                           int32_t* n_fallback, void* stream);
-/* Checkpoint: master weights and Adam state in a flat file with a header and a CRC-32.
+/* Checkpoint: master weights, Adam state and the pooling in a flat file with a header and a
+   CRC-32 (files written before the pooling field existed load as max pooling).
    mss_prop_load rejects (MSS_EINVAL, model unchanged) a file with another header or size, a
    truncated file or a CRC mismatch. */
 MSS_API mss_status mss_prop_save(const mss_prop* p, const char* path);

@@ -2,7 +2,9 @@
 
 Plain numpy (fp64) statement of the proposal network and its training loss; loaded only by
 tests.  The network: one-hot bases (N = all zero) -> 4 x [conv1d, kernel 7, "same" zero
-padding, 128 channels, bias, ReLU] -> max over positions -> L2 normalisation (+1e-6).
+padding, 128 channels, bias, ReLU] -> pool over positions -> L2 normalisation (+1e-6).
+The pool is the maximum (first maximum kept) or, with pooling="mean", the mean over the
+sequence's positions (the other reading of how a window's features become one vector).
 Rounding points follow the documented precision of the path: layers 2..4 use BF16 weights,
 the activations between layers are stored in BF16 (round to nearest even), accumulation is
 exact here (fp64).  With rounding=False everything is fp64 (used by the finite-difference
@@ -55,8 +57,9 @@ def _shift(a: np.ndarray, t: int) -> np.ndarray:
     return out
 
 
-def forward(params, codes: np.ndarray, rounding: bool = True):
+def forward(params, codes: np.ndarray, rounding: bool = True, pooling: str = "max"):
     """Embedding of one code sequence (values 0..3 bases, 4 = N).  Returns (emb, cache)."""
+    assert pooling in ("max", "mean")
     w1, b1, ws, bs = unpack(params)
     x = np.asarray(codes, dtype=np.int64)
     L = x.shape[0]
@@ -75,7 +78,10 @@ def forward(params, codes: np.ndarray, rounding: bool = True):
         a = rnd(np.maximum(z, 0.0))
         acts.append(a)
         pres.append(z)
-    if L > 0:
+    if L > 0 and pooling == "mean":
+        arg = np.zeros(C, dtype=np.int64)
+        v = a.sum(axis=0) / L
+    elif L > 0:
         arg = np.argmax(a, axis=0)          # first maximum
         v = a[arg, np.arange(C)]
     else:
@@ -86,15 +92,17 @@ def forward(params, codes: np.ndarray, rounding: bool = True):
     return e, (acts, pres, arg, v, nrm)
 
 
-def backward(params, codes: np.ndarray, demb: np.ndarray, rounding: bool = True) -> np.ndarray:
+def backward(params, codes: np.ndarray, demb: np.ndarray, rounding: bool = True, pooling: str = "max") -> np.ndarray:
     """Gradient of <demb, emb(codes)> with respect to the flat parameters (fp64)."""
     w1, b1, ws, bs = unpack(params)
-    e, (acts, pres, arg, v, nrm) = forward(params, codes, rounding)
+    e, (acts, pres, arg, v, nrm) = forward(params, codes, rounding, pooling)
     de = np.asarray(demb, dtype=np.float64)
     dv = (de - e * np.dot(e, de)) / nrm
     L = acts[0].shape[0]
     g = np.zeros_like(acts[4])
-    if L > 0:
+    if L > 0 and pooling == "mean":
+        g[:, :] = dv[None, :] / L           # every position carries 1/L of the pooled value
+    elif L > 0:
         g[arg, np.arange(C)] = dv
     grads_w, grads_b = [None] * 3, [None] * 3
     for l in range(2, -1, -1):     # layers 4, 3, 2

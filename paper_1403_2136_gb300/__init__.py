@@ -33,7 +33,7 @@ EXPORTS = ("mss_load_genome", "mss_load_genome_device", "mss_get_info", "mss_set
            "mss_get_read_step", "mss_set_tune",
            "mss_get_tune", "mss_map_reads", "mss_map_reads_device", "nw_align", "nw_align_device", "nw_align_device_noalloc", "mss_map_align", "mss_sync",
            "mss_autotune", "mss_scan_timing", "mss_scan_time_ms", "mss_launch_count", "mss_genome_codes", "mss_probe_pipes", "mss_check_wait_timeout", "mss_prop_create", "mss_prop_free", "mss_prop_param_count",
-           "mss_prop_get_params", "mss_prop_set_params", "mss_prop_read_codes", "mss_prop_window_codes",
+           "mss_prop_get_params", "mss_prop_set_params", "mss_prop_set_pooling", "mss_prop_get_pooling", "mss_prop_read_codes", "mss_prop_window_codes",
            "mss_prop_embed_device", "mss_prop_grad_device", "mss_prop_train_step", "mss_prop_build_index",
            "mss_map_reads_proposed", "mss_prop_save", "mss_prop_load", "mss_prop_launch_count", "mss_free",
            "mss_map_reads_quals_device", "nw_align_quals_device", "mss_mapq", "mss_format_sam", "mss_last_error")
@@ -116,6 +116,8 @@ def load_library(path: str = LIB_PATH):
         "mss_prop_param_count": ([], i64),
         "mss_prop_get_params": ([P, P, i64], i32),
         "mss_prop_set_params": ([P, P, i64], i32),
+        "mss_prop_set_pooling": ([P, i32], i32),
+        "mss_prop_get_pooling": ([P], i32),
         "mss_prop_read_codes": ([P, P, P, P, P, i32, i32, P, P, P], i32),
         "mss_prop_window_codes": ([P, P, P, i32, i32, i32, P, P, P], i32),
         "mss_prop_embed_device": ([P, P, P, i32, i32, i32, P, P], i32),
@@ -451,6 +453,20 @@ class Proposal:
     def set_params(self, w: np.ndarray):
         w = np.ascontiguousarray(w, dtype=np.float32)
         _check(_lib.mss_prop_set_params(self._h, _host_ptr(w), w.shape[0]), "mss_prop_set_params")
+
+    POOLINGS = {"max": 0, "mean": 1}
+
+    @property
+    def pooling(self) -> str:
+        """How the last layer's positions become one vector: "max" or "mean"."""
+        v = int(_lib.mss_prop_get_pooling(self._h))
+        return {i: k for k, i in self.POOLINGS.items()}[v]
+
+    @pooling.setter
+    def pooling(self, name: str):
+        if name not in self.POOLINGS:
+            raise ValueError(f"pooling must be one of {sorted(self.POOLINGS)}")
+        _check(_lib.mss_prop_set_pooling(self._h, self.POOLINGS[name]), "mss_prop_set_pooling")
 
     def read_codes(self, d_reads, d_offsets, d_idx, d_strand, n, ld, d_codes, d_lens, stream=None):
         _check(_lib.mss_prop_read_codes(self._h, _host_ptr(d_reads), _host_ptr(d_offsets), _host_ptr(d_idx),

@@ -3,14 +3,16 @@
 // per read so that the exact scan runs only on the top K.
 //
 // Network: one-hot bases (N = all zero) -> 4 x [conv1d k=7 "same", 128 channels, bias, ReLU]
-// -> max over positions -> L2 normalisation.  Weights BF16, accumulation FP32.
+// -> pool over positions (maximum, or mean as an option) -> L2 normalisation.  Weights BF16,
+// accumulation FP32.
 //
 // Kernels here (the 128 -> 128 conv itself, forward and backward-data, runs on the
 // fifth-generation tensor cores in conv_tc.cu, its weight gradient in wgrad_tc.cu, the read x
 // fragment score GEMM with its fused top K in score_tc.cu):
 //   k_embed_l1      first layer (4 -> 128) as a gather-sum of per-base weight rows
-//   k_pool_norm     max over positions (first argmax kept), L2 norm
-//   k_pool_norm_bwd gradient of the norm routed to the argmax positions
+//   k_pool_norm     max (first argmax kept) or mean over positions, L2 norm
+//   k_pool_norm_bwd gradient of the norm routed to the argmax positions (max) or spread
+//                   over the positions with weight 1 / length (mean)
 //   k_l1_wgrad      first-layer weight/bias gradients; k_bias_grad: bias gradients
 //   k_ce_loss       softmax cross-entropy of read-vs-candidate logits and its gradients
 //   k_adamw         AdamW on FP32 master weights, refreshing the BF16 copies
@@ -135,32 +137,46 @@ __global__ void k_l1_wgrad(const uint8_t* __restrict__ codes, const int32_t* __r
 }
 
 // ------------------------------------------------------------------------------------------
-// max over positions p < len (first maximum), L2 norm.  One CTA (128 threads) per sequence.
-// max over the positions of each channel (first argmax kept), then the L2 norm.  CTA = one
-// sequence, 256 threads = 16 position lanes x 16 groups of 8 channels; the lanes' maxima
-// merge with ties going to the lower position, so the result is the first maximum.
+// pool over the positions p < len of each channel, then the L2 norm.  CTA = one sequence,
+// 256 threads = 16 position lanes x 16 groups of 8 channels.  Max: the lanes' maxima merge
+// with ties going to the lower position, so the result is the first maximum.  Mean: the
+// lanes' FP32 sums add in lane order and the total is divided by len.
 __global__ void __launch_bounds__(256) k_pool_norm(const __nv_bfloat16* __restrict__ act,
                                                    const int32_t* __restrict__ lens, int32_t rows,
                                                    float* __restrict__ emb, float* __restrict__ norms,
-                                                   int32_t* __restrict__ argmax) {
+                                                   int32_t* __restrict__ argmax, int32_t mean) {
   const int n = blockIdx.x, tid = threadIdx.x;
   const int g = tid & 15, pl = tid >> 4;
   const int len = lens[n];
   float best[8];
   int bi[8];
 #pragma unroll
-  for (int j = 0; j < 8; ++j) best[j] = -1.f, bi[j] = 0;
+  for (int j = 0; j < 8; ++j) best[j] = mean ? 0.f : -1.f, bi[j] = 0;
   const __nv_bfloat16* an = act + ((int64_t)n * rows + 3) * kPropC + 8 * g;
+  if (mean) {
 #pragma unroll 4
-  for (int p = pl; p < len; p += 16) {
-    const uint4 u = *reinterpret_cast<const uint4*>(an + (int64_t)p * kPropC);
-    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+    for (int p = pl; p < len; p += 16) {
+      const uint4 u = *reinterpret_cast<const uint4*>(an + (int64_t)p * kPropC);
+      const uint32_t w[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162*>(&w[j]);
-      const float v0 = __bfloat162float(h.x), v1 = __bfloat162float(h.y);
-      if (v0 > best[2 * j]) best[2 * j] = v0, bi[2 * j] = p;
-      if (v1 > best[2 * j + 1]) best[2 * j + 1] = v1, bi[2 * j + 1] = p;
+      for (int j = 0; j < 4; ++j) {
+        const __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162*>(&w[j]);
+        best[2 * j] += __bfloat162float(h.x);
+        best[2 * j + 1] += __bfloat162float(h.y);
+      }
+    }
+  } else {
+#pragma unroll 4
+    for (int p = pl; p < len; p += 16) {
+      const uint4 u = *reinterpret_cast<const uint4*>(an + (int64_t)p * kPropC);
+      const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162*>(&w[j]);
+        const float v0 = __bfloat162float(h.x), v1 = __bfloat162float(h.y);
+        if (v0 > best[2 * j]) best[2 * j] = v0, bi[2 * j] = p;
+        if (v1 > best[2 * j + 1]) best[2 * j + 1] = v1, bi[2 * j + 1] = p;
+      }
     }
   }
   __shared__ float s_best[16][kPropC];
@@ -172,10 +188,16 @@ __global__ void __launch_bounds__(256) k_pool_norm(const __nv_bfloat16* __restri
   const int co = tid;
   float b = -1.f;
   int bp = 0;
-  for (int l = 0; l < 16; ++l) {
-    const float v = s_best[l][co];
-    const int q = s_bi[l][co];
-    if (v > b || (v == b && v >= 0.f && q < bp)) b = v, bp = q;
+  if (mean) {
+    b = 0.f;
+    for (int l = 0; l < 16; ++l) b += s_best[l][co];
+    if (len > 0) b /= (float)len;
+  } else {
+    for (int l = 0; l < 16; ++l) {
+      const float v = s_best[l][co];
+      const int q = s_bi[l][co];
+      if (v > b || (v == b && v >= 0.f && q < bp)) b = v, bp = q;
+    }
   }
   if (len <= 0) b = 0.f, bp = 0;
   __shared__ float red[4];
@@ -190,11 +212,13 @@ __global__ void __launch_bounds__(256) k_pool_norm(const __nv_bfloat16* __restri
   if (norms && co == 0) norms[n] = nrm;
 }
 
-// gradient through the L2 norm and the max pool: g4[n][argmax + 3][co] = de_raw if act > 0
+// gradient through the L2 norm and the pool, masked by the last ReLU (g4 holds zeros on
+// entry): max, g4[n][argmax + 3][co] = de_raw where act > 0; mean, g4[n][p + 3][co] =
+// de_raw / len at every p < len where act > 0
 __global__ void k_pool_norm_bwd(const float* __restrict__ emb, const float* __restrict__ demb,
                                 const float* __restrict__ norms, const int32_t* __restrict__ argmax,
                                 const __nv_bfloat16* __restrict__ act, const int32_t* __restrict__ lens, int32_t rows,
-                                __nv_bfloat16* __restrict__ g4) {
+                                __nv_bfloat16* __restrict__ g4, int32_t mean) {
   const int n = blockIdx.x, co = threadIdx.x;
   __shared__ float red[4];
   const float e = emb[n * kPropC + co], de = demb[n * kPropC + co];
@@ -205,7 +229,16 @@ __global__ void k_pool_norm_bwd(const float* __restrict__ emb, const float* __re
   __syncthreads();
   dot = red[0] + red[1] + red[2] + red[3];
   const float draw = (de - e * dot) / norms[n];
-  if (lens[n] <= 0) return;
+  const int len = lens[n];
+  if (len <= 0) return;
+  if (mean) {
+    const __nv_bfloat16 gv = __float2bfloat16(draw / (float)len);
+    for (int p = 0; p < len; ++p) {
+      const int64_t o = ((int64_t)n * rows + p + 3) * kPropC + co;
+      if (__bfloat162float(act[o]) > 0.f) g4[o] = gv;
+    }
+    return;
+  }
   const int p = argmax[n * kPropC + co];
   const int64_t o = ((int64_t)n * rows + p + 3) * kPropC + co;
   if (__bfloat162float(act[o]) > 0.f) g4[o] = __float2bfloat16(draw);
@@ -467,15 +500,15 @@ cudaError_t prop_l1_wgrad(const uint8_t* codes, const int32_t* lens, int32_t ld,
 }
 
 cudaError_t prop_pool_norm(const __nv_bfloat16* act, const int32_t* lens, int32_t n, int32_t rows, float* emb,
-                           float* norms, int32_t* argmax, cudaStream_t s) {
-  k_pool_norm<<<n, 256, 0, s>>>(act, lens, rows, emb, norms, argmax);
+                           float* norms, int32_t* argmax, int32_t mean, cudaStream_t s) {
+  k_pool_norm<<<n, 256, 0, s>>>(act, lens, rows, emb, norms, argmax, mean);
   return cudaGetLastError();
 }
 
 cudaError_t prop_pool_norm_bwd(const float* emb, const float* demb, const float* norms, const int32_t* argmax,
                                const __nv_bfloat16* act, const int32_t* lens, int32_t n, int32_t rows,
-                               __nv_bfloat16* g4, cudaStream_t s) {
-  k_pool_norm_bwd<<<n, kPropC, 0, s>>>(emb, demb, norms, argmax, act, lens, rows, g4);
+                               __nv_bfloat16* g4, int32_t mean, cudaStream_t s) {
+  k_pool_norm_bwd<<<n, kPropC, 0, s>>>(emb, demb, norms, argmax, act, lens, rows, g4, mean);
   return cudaGetLastError();
 }
 

@@ -45,10 +45,10 @@ cudaError_t prop_bias_grad(const __nv_bfloat16* g, const int32_t* lens, float* d
 cudaError_t prop_l1_wgrad(const uint8_t* codes, const int32_t* lens, int32_t ld, const __nv_bfloat16* g, float* dw1,
                           float* db1, int32_t n, int32_t rows, cudaStream_t s);
 cudaError_t prop_pool_norm(const __nv_bfloat16* act, const int32_t* lens, int32_t n, int32_t rows, float* emb,
-                           float* norms, int32_t* argmax, cudaStream_t s);
+                           float* norms, int32_t* argmax, int32_t mean, cudaStream_t s);
 cudaError_t prop_pool_norm_bwd(const float* emb, const float* demb, const float* norms, const int32_t* argmax,
                                const __nv_bfloat16* act, const int32_t* lens, int32_t n, int32_t rows,
-                               __nv_bfloat16* g4, cudaStream_t s);
+                               __nv_bfloat16* g4, int32_t mean, cudaStream_t s);
 cudaError_t prop_ce_loss(const float* r, const float* c, const int32_t* label, int32_t B, int32_t C, float inv_temp,
                          float* loss, float* dr, float* dc, float scale, cudaStream_t s);
 cudaError_t prop_adamw(float* w, const float* g, float* m1, float* m2, __nv_bfloat16* wb, int64_t count, float lr,

@@ -87,6 +87,7 @@ struct mss_prop {
   Buf scores, cand, cand_s, cand_x, emb_reads, breads, part_key, part_f;
   int64_t step = 0;
   int64_t launches = 0;
+  int32_t pooling = MSS_POOL_MAX;   // how a sequence's positions become one vector
 };
 
 namespace {
@@ -118,7 +119,7 @@ mss_status forward(mss_prop* p, const uint8_t* codes, const int32_t* lens, int32
                      a.act[l - 1].as<__nv_bfloat16>(), n, rows, 0, p->err.as<int32_t>(), s),
         "conv layer");
   PCK(prop_pool_norm(a.act[3].as<__nv_bfloat16>(), lens, n, rows, a.emb.as<float>(), a.norms.as<float>(),
-                     a.argmax.as<int32_t>(), s),
+                     a.argmax.as<int32_t>(), p->pooling == MSS_POOL_MEAN, s),
       "pool");
   p->launches += 6;
   return MSS_OK;
@@ -137,7 +138,7 @@ mss_status backward(mss_prop* p, const uint8_t* codes, const int32_t* lens, int3
   __nv_bfloat16* gcur = p->g[0].as<__nv_bfloat16>();
   __nv_bfloat16* gnext = p->g[1].as<__nv_bfloat16>();
   PCK(prop_pool_norm_bwd(a.emb.as<float>(), demb, a.norms.as<float>(), a.argmax.as<int32_t>(),
-                         a.act[3].as<__nv_bfloat16>(), lens, n, rows, gcur, s),
+                         a.act[3].as<__nv_bfloat16>(), lens, n, rows, gcur, p->pooling == MSS_POOL_MEAN, s),
       "pool backward");
   p->launches += 1;
   for (int l = 4; l >= 2; --l) {
@@ -258,6 +259,15 @@ mss_status mss_prop_set_params(mss_prop* p, const float* host, int64_t n) {
 }
 
 int64_t mss_prop_param_count(void) { return kPropParams; }
+
+mss_status mss_prop_set_pooling(mss_prop* p, int32_t pooling) {
+  if (check_prop(p)) return set_error(MSS_EINVAL, "null proposal model");
+  if (pooling != MSS_POOL_MAX && pooling != MSS_POOL_MEAN) return set_error(MSS_EINVAL, "unknown pooling");
+  p->pooling = pooling;
+  return MSS_OK;
+}
+
+int32_t mss_prop_get_pooling(const mss_prop* p) { return p ? p->pooling : -1; }
 
 mss_status mss_prop_embed_device(mss_prop* p, const uint8_t* d_codes, const int32_t* d_lens, int32_t ld, int32_t n,
                                  int32_t maxlen, float* d_emb, void* stream) {
@@ -542,7 +552,8 @@ mss_status mss_prop_window_codes(mss_prop* p, const mss_ctx* ctx, const int64_t*
 
 int64_t mss_prop_launch_count(const mss_prop* p) { return p ? p->launches : -1; }
 
-// checkpoint: "MSSPROP1", param count, step, then master weights, Adam moments; CRC-32 of all
+// checkpoint: "MSSPROP2", param count, step, pooling, then master weights, Adam moments;
+// CRC-32 of all.  "MSSPROP1" files (no pooling field: max pooling) are still read.
 mss_status mss_prop_save(const mss_prop* p, const char* path) {
   if (check_prop(p) || !path) return set_error(MSS_EINVAL, "null argument");
   std::vector<float> buf((size_t)kPropParams * 3);
@@ -551,8 +562,8 @@ mss_status mss_prop_save(const mss_prop* p, const char* path) {
   PCK(cudaMemcpy(buf.data() + 2 * kPropParams, p->m2.p, (size_t)kPropParams * 4, cudaMemcpyDeviceToHost), "read");
   FILE* f = fopen(path, "wb");
   if (!f) return set_error(MSS_EINVAL, "cannot open checkpoint for writing");
-  const char magic[8] = {'M', 'S', 'S', 'P', 'R', 'O', 'P', '1'};
-  const int64_t hdr[2] = {kPropParams, p->step};
+  const char magic[8] = {'M', 'S', 'S', 'P', 'R', 'O', 'P', '2'};
+  const int64_t hdr[3] = {kPropParams, p->step, (int64_t)p->pooling};
   uint32_t crc = crc32_bytes(hdr, sizeof(hdr));
   crc = crc32_bytes(buf.data(), buf.size() * 4, crc);
   bool ok = fwrite(magic, 1, 8, f) == 8 && fwrite(hdr, sizeof(hdr), 1, f) == 1 &&
@@ -566,21 +577,25 @@ mss_status mss_prop_load(mss_prop* p, const char* path) {
   FILE* f = fopen(path, "rb");
   if (!f) return set_error(MSS_EINVAL, "cannot open checkpoint");
   char magic[8];
-  int64_t hdr[2];
+  int64_t hdr[3] = {0, 0, MSS_POOL_MAX};
   std::vector<float> buf((size_t)kPropParams * 3);
   uint32_t crc_file = 0;
-  bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, "MSSPROP1", 8) == 0 && fread(hdr, sizeof(hdr), 1, f) == 1 &&
-            hdr[0] == kPropParams && fread(buf.data(), 4, buf.size(), f) == buf.size() &&
-            fread(&crc_file, 4, 1, f) == 1;
+  bool ok = fread(magic, 1, 8, f) == 8;
+  const bool v1 = ok && memcmp(magic, "MSSPROP1", 8) == 0, v2 = ok && memcmp(magic, "MSSPROP2", 8) == 0;
+  const size_t nh = v1 ? 2 : 3;
+  ok = (v1 || v2) && fread(hdr, sizeof(int64_t), nh, f) == nh && hdr[0] == kPropParams &&
+       (hdr[2] == MSS_POOL_MAX || hdr[2] == MSS_POOL_MEAN) && fread(buf.data(), 4, buf.size(), f) == buf.size() &&
+       fread(&crc_file, 4, 1, f) == 1;
   fclose(f);
   if (!ok) return set_error(MSS_EINVAL, "not a proposal checkpoint (header, size or truncation)");
-  uint32_t crc = crc32_bytes(hdr, sizeof(hdr));
+  uint32_t crc = crc32_bytes(hdr, nh * sizeof(int64_t));
   crc = crc32_bytes(buf.data(), buf.size() * 4, crc);
   if (crc != crc_file) return set_error(MSS_EINVAL, "checkpoint CRC mismatch");
   PCK(cudaMemcpy(p->w32.p, buf.data(), (size_t)kPropParams * 4, cudaMemcpyHostToDevice), "write");
   PCK(cudaMemcpy(p->m1.p, buf.data() + kPropParams, (size_t)kPropParams * 4, cudaMemcpyHostToDevice), "write");
   PCK(cudaMemcpy(p->m2.p, buf.data() + 2 * kPropParams, (size_t)kPropParams * 4, cudaMemcpyHostToDevice), "write");
   p->step = hdr[1];
+  p->pooling = (int32_t)hdr[2];
   return refresh_bf16(p, nullptr);
 }
 

@@ -10,11 +10,11 @@
 // taps (0-3 or 4-6) whose FP32 accumulators (128 columns each) fill the tensor memory.  Per
 // tile its 128 threads copy, with 16-byte cp.async, the input rows of the tile's positions
 // shifted by the group's first tap (131 rows, padded to 136) and the 128 gradient rows into a
-// two-stage ring; each 16-byte chunk (8 channels of one row) lands at
+// three-stage ring, two tiles ahead of the MMAs; each 16-byte chunk (8 channels of one row) lands at
 // channel-group * stride + row * 16, so that rows are 16 bytes apart throughout and a tap's
 // shift is a start-address offset of 16 bytes per row.  One thread issues, per tap, eight
-// tcgen05.mma (K = 16 positions each) and commits them on the stage's mbarrier; the copy of
-// the stage after next waits for it.  At the end the four warps read their 32 accumulator
+// tcgen05.mma (K = 16 positions each) and commits them on the stage's mbarrier; the next copy
+// into that stage waits for it.  At the end the four warps read their 32 accumulator
 // lanes (input channels) back and add them to dw with FP32 atomics.  Every wait is bounded.
 #include <cuda_bf16.h>
 
@@ -39,7 +39,8 @@ constexpr uint32_t kWgBStride = kWgTile * 16;             // the same for B
 constexpr uint32_t kWgABytes = 16 * kWgAStride;           // 34,816
 constexpr uint32_t kWgBBytes = 16 * kWgBStride;           // 32,768
 constexpr uint32_t kWgStage = kWgABytes + kWgBBytes;
-constexpr uint32_t kWgSmem = 2 * kWgStage + 64;           // two stages, mbarriers, TMEM slot
+constexpr int kWgStages = 3;                              // copies two tiles ahead
+constexpr uint32_t kWgSmem = kWgStages * kWgStage + 64;   // stages, mbarriers, TMEM slot
 constexpr uint64_t kWgWaitNs = 2000000000ull;
 // MN-major operands without swizzling: core matrices of 8 rows (K) x 16 bytes (8 MN
 // elements); the descriptor's leading offset is the distance between core matrices adjacent
@@ -59,8 +60,8 @@ __global__ void __launch_bounds__(kWgThreads, 1)
                     const int32_t* __restrict__ lens, float* __restrict__ dw, int32_t n_seq, int32_t rows,
                     int32_t tiles_per_cta, int32_t* err) {
   extern __shared__ __align__(1024) uint8_t sm[];
-  uint64_t* done = reinterpret_cast<uint64_t*>(sm + 2 * kWgStage);   // [2]
-  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(sm + 2 * kWgStage + 16);
+  uint64_t* done = reinterpret_cast<uint64_t*>(sm + kWgStages * kWgStage);   // [kWgStages]
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(sm + kWgStages * kWgStage + 8 * kWgStages);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int t0 = blockIdx.y * kWgTapsPerCta;
   const int ntaps = min(kWgTapsPerCta, kPropTaps - t0);
@@ -70,8 +71,7 @@ __global__ void __launch_bounds__(kWgThreads, 1)
   const int64_t last = min(total, first + tiles_per_cta);
 
   if (tid == 0) {
-    mbar_init(&done[0], 1);
-    mbar_init(&done[1], 1);
+    for (int k = 0; k < kWgStages; ++k) mbar_init(&done[k], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -83,43 +83,71 @@ __global__ void __launch_bounds__(kWgThreads, 1)
   tc_fence_after();
   const uint32_t tmem = *s_tmem;
 
-  bool ok = true;
-  int issued = 0;  // tiles whose MMAs have been issued (and committed on done[tile & 1])
-  for (int64_t tile = first; tile < last && ok; ++tile) {
+  // tiles past a sequence's length carry zero gradients: skip them (the same for every thread)
+  auto next_live = [&](int64_t tile) {
+    while (tile < last) {
+      const int n = (int)(tile / tiles_per_seq);
+      if ((int)(tile - (int64_t)n * tiles_per_seq) * kWgTile < lens[n]) break;
+      ++tile;
+    }
+    return tile;
+  };
+  // copy tile `tile` into stage s: the input rows p0 + t0 + r (buffer rows: position
+  // p0 + t0 + r - 3), r < ntaps - 1 + 128 (the last tile's last row is the sequence's last buffer
+  // row; the pad rows up to 135 are never read by an MMA of a tap of this group), and the
+  // gradient rows of positions p0 .. p0 + 127 (buffer rows p0 + 3 ...)
+  auto stage_copy = [&](int64_t tile, int s) {
     const int n = (int)(tile / tiles_per_seq);
     const int p0 = (int)(tile - (int64_t)n * tiles_per_seq) * kWgTile;
-    if (p0 >= lens[n]) continue;  // uniform across the CTA: gradients past the length are zero
-    const int s = issued & 1;
-    // the stage's previous tile (issued - 2) must have finished reading it
-    if (issued >= 2) ok = mbar_wait(&done[s], (uint32_t)(((issued - 2) >> 1) & 1), kWgWaitNs);
-    if (!__syncthreads_and(ok)) {
-      ok = false;
-      break;
-    }
-    uint8_t* sA = sm + s * kWgStage;
-    uint8_t* sB = sA + kWgABytes;
-    // input rows p0 + t0 + r (buffer rows: position p0 + t0 + r - 3), r < ntaps - 1 + 128:
-    // the last tile's last row is the sequence's last buffer row; the pad rows up to 135 are
-    // never read by an MMA of a tap of this group
+    const uint32_t sA = smem_u32(sm + s * kWgStage), sB = sA + kWgABytes;
     const __nv_bfloat16* ia = in + ((int64_t)n * rows + p0 + t0) * kPropC;
     const int arows = ntaps - 1 + kWgTile;
     for (int e = tid; e < arows * 16; e += kWgThreads) {
       const int r = e >> 4, c = e & 15;
-      cp_async16_wg(smem_u32(sA) + c * kWgAStride + r * 16, ia + (int64_t)r * kPropC + c * 8);
+      cp_async16_wg(sA + c * kWgAStride + r * 16, ia + (int64_t)r * kPropC + c * 8);
     }
-    // gradient rows of positions p0 .. p0 + 127 (buffer rows p0 + 3 ...)
     const __nv_bfloat16* gb = g + ((int64_t)n * rows + p0 + 3) * kPropC;
     for (int e = tid; e < kWgTile * 16; e += kWgThreads) {
       const int r = e >> 4, c = e & 15;
-      cp_async16_wg(smem_u32(sB) + c * kWgBStride + r * 16, gb + (int64_t)r * kPropC + c * 8);
+      cp_async16_wg(sB + c * kWgBStride + r * 16, gb + (int64_t)r * kPropC + c * 8);
+    }
+  };
+
+  // Live tile k goes to stage k mod kWgStages and its MMAs commit on done[k mod kWgStages].
+  // Every thread commits one cp.async group per prologue slot and per loop iteration (empty
+  // once the tiles run out), so that group k holds live tile k's copies.
+  bool ok = true;
+  int64_t fetch = next_live(first);  // the next live tile to copy
+  int copied = 0, issued = 0;         // live tiles copied / whose MMAs were issued
+  for (int k = 0; k < kWgStages - 1; ++k) {
+    if (fetch < last) {
+      stage_copy(fetch, k);
+      fetch = next_live(fetch + 1);
+      ++copied;
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
+  }
+  while (issued < copied) {
+    const int s = issued % kWgStages;
+    if (fetch < last) {
+      // copied == issued + kWgStages - 1: the stage to refill was last read by tile issued - 1
+      if (issued >= 1)
+        ok = mbar_wait(&done[(issued - 1) % kWgStages], (uint32_t)(((issued - 1) / kWgStages) & 1), kWgWaitNs);
+      if (!__syncthreads_and(ok)) {
+        ok = false;
+        break;
+      }
+      stage_copy(fetch, copied % kWgStages);
+      fetch = next_live(fetch + 1);
+      ++copied;
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group %0;" ::"n"(kWgStages - 1) : "memory");  // group `issued` landed
     fence_proxy_async_smem();  // the copies are visible to the tensor cores
     __syncthreads();
     if (tid == 0) {
       tc_fence_after();
-      const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+      const uint32_t a0 = smem_u32(sm + s * kWgStage), b0 = a0 + kWgABytes;
       for (int j = 0; j < ntaps; ++j) {
 #pragma unroll
         for (int kk = 0; kk < kWgTile / 16; ++kk)
@@ -131,10 +159,11 @@ __global__ void __launch_bounds__(kWgThreads, 1)
     }
     ++issued;
   }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");  // no copy in flight past this point
   // wait for the last committed tile of each stage (bounded), then read the accumulators
   bool drained = true;
-  for (int k = issued - 1; k >= 0 && k >= issued - 2; --k)
-    if (!mbar_wait(&done[k & 1], (uint32_t)((k >> 1) & 1), kWgWaitNs)) drained = false;
+  for (int k = issued - 1; k >= 0 && k >= issued - kWgStages; --k)
+    if (!mbar_wait(&done[k % kWgStages], (uint32_t)((k / kWgStages) & 1), kWgWaitNs)) drained = false;
   if (!ok || !drained) {
     if (tid == 0) atomicOr(err, ERR_TIMEOUT);
   } else if (issued > 0) {

@@ -229,6 +229,8 @@ def main(argv=None):
     ap.add_argument("--subsample", type=int, default=20_000, help="exhaustive subsample of --scale-reads")
     ap.add_argument("--checkpoint", type=str, default="", help="save the trained weights here")
     ap.add_argument("--load", type=str, default="", help="start from these weights")
+    ap.add_argument("--pooling", choices=["max", "mean"], default="max",
+                    help="how the last layer's positions become one vector (a checkpoint's own setting wins)")
     args = ap.parse_args(argv)
     log = lambda m: print(m, file=sys.stderr, flush=True)  # noqa: E731
 
@@ -244,6 +246,7 @@ def main(argv=None):
     label_s = time.perf_counter() - t0
     log(f"labels for {tr.count} reads on {genome.shape[0]} bp in {label_s:.1f} s")
     prop = Proposal(seed=1)
+    prop.pooling = args.pooling
     if args.load:
         prop.load(args.load)
     t0 = time.perf_counter()
@@ -262,7 +265,7 @@ def main(argv=None):
         scale = at_scale(torch, gen, prop, args, rspec, max_len, F, taus, log)
         print(json.dumps({"metric": "learned proposal at scale (no fallback) vs an exhaustive subsample",
                           "train_genome": wl.name, "train_reads": tr.count, "train_steps": args.steps,
-                          "loaded": args.load or None, **scale}), flush=True)
+                          "pooling": prop.pooling, "loaded": args.load or None, **scale}), flush=True)
         prop.close()
         return
     evals = []
@@ -304,7 +307,7 @@ def main(argv=None):
     line = {"metric": "learned proposal + exact rescoring vs exhaustive scan (top-1 agreement, recall, speedup)",
             "train_genome": wl.name, "train_genome_bp": int(genome.shape[0]), "frag_len": F,
             "read_shape": args.read_shape, "train_reads": tr.count, "train_steps": args.steps, "batch": args.batch,
-            "mine_every": args.mine_every, "hard": args.hard if args.mine_every else 0,
+            "mine_every": args.mine_every, "hard": args.hard if args.mine_every else 0, "pooling": prop.pooling,
             "loss_first": round(losses[0], 4) if losses else None,
             "loss_last": round(float(np.mean(losses[-20:])), 4) if losses else None,
             "loss_curve": [round(float(np.mean(c)), 4) for c in np.array_split(np.asarray(losses), min(10, len(losses)))]

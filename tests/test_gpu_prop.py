@@ -5,6 +5,7 @@ the exact path:
   (bounded in BF16 ulps: at most 1% of the coordinates off by more than one ulp);
 * parameter gradients vs the oracle's backward pass (relative error of the whole vector and of
   every parameter block, 1e-2 / 1.5e-2);
+* the mean-pooling option: embeddings, gradients and its checkpoint round trip;
 * input codes (reads, both strands; genome windows) bit-exact;
 * proposal + exact rescoring: with K = all fragments, and with every read falling back, the
   result equals the exhaustive scan bit for bit; with small K the rescored best/second equal
@@ -151,6 +152,77 @@ def test_gradients_match_oracle(mss):
         if np.linalg.norm(w_) > 1e-6:
             assert np.linalg.norm(g - w_) / np.linalg.norm(w_) < 1.5e-2, (o, size)
         o += size
+    prop.close()
+
+
+def test_mean_pooling_matches_oracle(mss):
+    """The mean-pooling option: embeddings (lengths 1 to 700, N bases, a sequence longer than
+    a conv tile) against the oracle's mean pool with the same rounding points, the parameter
+    gradient of a batch against the oracle's backward pass, the setting's checks, and its
+    round trip through a checkpoint."""
+    import torch
+    prop = mss.Proposal(seed=7)
+    assert prop.pooling == "max"
+    with pytest.raises(ValueError):
+        prop.pooling = "sum"
+    assert mss.load_library().mss_prop_set_pooling(prop.handle, 2) == mss.MSS_EINVAL
+    prop.pooling = "mean"
+    assert prop.pooling == "mean"
+    params = random_params(51)
+    prop.set_params(params)
+    rng = np.random.default_rng(52)
+    lens = np.array([1, 2, 7, 31, 100, 129, 250, 700, 64, 333], dtype=np.int32)
+    ld = 704
+    codes = np.full((lens.size, ld), 4, np.uint8)
+    for i, L in enumerate(lens):
+        codes[i, :L] = rng.choice(5, size=L, p=[.24, .24, .24, .24, .04])
+    d_emb = torch.zeros(lens.size * 128, dtype=torch.float32, device="cuda")
+    prop.embed(dev(codes), dev(lens), ld, lens.size, int(lens.max()), d_emb)
+    torch.cuda.synchronize()
+    got = d_emb.cpu().numpy().reshape(-1, 128)
+    p64 = params.astype(np.float64)
+    for i, L in enumerate(lens):
+        want, _ = po.forward(p64, codes[i, :L], pooling="mean")
+        mx, _ = po.forward(p64, codes[i, :L])
+        assert np.abs(got[i] - want).max() < 3e-3, (i, L, np.abs(got[i] - want).max())
+        assert np.dot(got[i], want) > 0.99999
+        if L > 1:
+            assert np.abs(want - mx).max() > 1e-2     # the two poolings differ
+    m = lens.size
+    demb = rng.normal(size=(m, 128)).astype(np.float32)
+    d_grad = torch.zeros(po.param_count(), dtype=torch.float32, device="cuda")
+    prop.grad(dev(codes), dev(lens), ld, m, int(lens.max()), dev(demb), d_grad)
+    torch.cuda.synchronize()
+    g = d_grad.cpu().numpy().astype(np.float64)
+    want = sum(po.backward(p64, codes[i, :L], demb[i], pooling="mean") for i, L in enumerate(lens))
+    assert np.linalg.norm(g - want) / np.linalg.norm(want) < 1e-2
+    o = 0
+    for size in [po.TAPS * 4 * po.C, po.C] + [po.TAPS * po.C * po.C, po.C] * 3:
+        gb, wb = g[o:o + size], want[o:o + size]
+        if np.linalg.norm(wb) > 1e-6:
+            assert np.linalg.norm(gb - wb) / np.linalg.norm(wb) < 1.5e-2, (o, size)
+        o += size
+    with tempfile.TemporaryDirectory() as td:
+        path = os.path.join(td, "mean.ckpt")
+        prop.save(path)
+        other = mss.Proposal(seed=8)
+        assert other.pooling == "max"
+        other.load(path)
+        assert other.pooling == "mean"
+        d_emb2 = torch.zeros_like(d_emb)
+        other.embed(dev(codes), dev(lens), ld, lens.size, int(lens.max()), d_emb2)
+        torch.cuda.synchronize()
+        assert torch.equal(d_emb2, d_emb)
+        # a file of the earlier format (magic "MSSPROP1", no pooling field) loads as max pooling
+        import zlib
+        hdr = np.array([po.param_count(), 5], dtype=np.int64).tobytes()
+        body = np.concatenate([params, np.zeros(2 * po.param_count(), np.float32)]).tobytes()
+        crc = (zlib.crc32(hdr + body) ^ 0xFFFFFFFF) & 0xFFFFFFFF
+        v1 = os.path.join(td, "v1.ckpt")
+        open(v1, "wb").write(b"MSSPROP1" + hdr + body + np.array([crc], np.uint32).tobytes())
+        other.load(v1)
+        assert other.pooling == "max" and np.array_equal(other.get_params(), params)
+        other.close()
     prop.close()
 
 

@@ -123,6 +123,12 @@ PROP_MUTANTS = {
     "backward_shift_direction": ("            s = t - 3\n            contrib", "            s = 3 - t\n            contrib"),
     # loss gradient not averaged over the batch
     "ce_not_averaged": ("    d /= B\n", ""),
+    # mean pooling: the sum instead of the mean
+    "mean_pool_not_divided": ("        v = a.sum(axis=0) / L\n", "        v = a.sum(axis=0)\n"),
+    # mean pooling backward: the 1/L factor dropped
+    "mean_pool_backward_not_divided": ("g[:, :] = dv[None, :] / L", "g[:, :] = dv[None, :]"),
+    # mean pooling over the padded length (one more row than the sequence)
+    "mean_pool_wrong_length": ("        v = a.sum(axis=0) / L\n", "        v = a.sum(axis=0) / (L + 1)\n"),
     # BF16 rounding: ties away from zero
     "bf16_ties_away": ("u = (u + 0x7FFF + ((u >> 16) & 1)) >> 16 << 16", "u = (u + 0x8000) >> 16 << 16"),
 }

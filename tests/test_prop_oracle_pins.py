@@ -5,6 +5,7 @@ import importlib.util
 import os
 
 import numpy as np
+import pytest
 
 if os.environ.get("MSS_PROP_ORACLE"):   # a variant with a planted mistake (tests/test_oracle_mutants.py)
     _spec = importlib.util.spec_from_file_location("prop_oracle_variant", os.environ["MSS_PROP_ORACLE"])
@@ -33,14 +34,15 @@ def test_all_n_sequence_uses_only_biases():
     assert np.allclose(acts[0], 0)   # N is the zero one-hot
 
 
-def test_backward_matches_finite_differences():
+@pytest.mark.parametrize("pooling", ["max", "mean"])
+def test_backward_matches_finite_differences(pooling):
     w = small_params(4, scale=0.3)
     codes = np.random.default_rng(5).integers(0, 4, size=18)
     demb = np.random.default_rng(6).normal(size=po.C)
-    g = po.backward(w, codes, demb, rounding=False)
+    g = po.backward(w, codes, demb, rounding=False, pooling=pooling)
 
     def f(wv):
-        e, _ = po.forward(wv, codes, rounding=False)
+        e, _ = po.forward(wv, codes, rounding=False, pooling=pooling)
         return float(np.dot(e, demb))
 
     rng = np.random.default_rng(7)
@@ -143,3 +145,39 @@ def test_forward_fixed_by_hand():
         o += po.TAPS * po.C * po.C + po.C
     _, (_, _, arg, v, _) = po.forward(q, codes)
     assert arg[0] == 3 and v[0] == 1.0
+
+
+def test_mean_pool_fixed_by_hand():
+    """Mean pooling on one-path networks: the pooled channel is the sum of the layer-4
+    outputs over the sequence's positions divided by its length, the other channels are
+    zero, and the embedding is the unit vector along channel 0."""
+    codes = np.array([1, 2, 0, 3, 1, 0, 2, 2, 1, 3, 3, 1, 0, 2])   # A at 2, 5 and 12; L = 14
+    # two taps 0: the A at 2 and 5 fire (value 1) at 8 and 11; the A at 12 falls outside
+    p = _one_path_params(1.0, (1.0, 1.0, 1.0), taps=(0, 0, 3, 3))
+    e, (_, _, _, v, nrm) = po.forward(p, codes, pooling="mean")
+    assert v[0] == 2 / 14 and np.all(v[1:] == 0)
+    assert nrm == v[0] + 1e-6 and e[0] == v[0] / (v[0] + 1e-6)
+    # the max pool of the same network keeps one of the two: 1
+    _, (_, _, _, vmax, _) = po.forward(p, codes)
+    assert vmax[0] == 1.0
+    # layer-2 weight 1.75: both firing positions carry 1.75, mean 3.5 / 14 = 0.25
+    p = _one_path_params(1.0, (1.75, 1.0, 1.0), taps=(0, 0, 3, 3))
+    _, (_, _, _, v, _) = po.forward(p, codes, pooling="mean")
+    assert v[0] == 0.25
+    # the layer-4 bias of channel 0 reaches the pooled value through the positions where
+    # layer 4's output is positive (8 and 11), each with weight 1 / L: its gradient is 2 / 14
+    # times the gradient at the pooled value (the normalisation's, pinned by finite
+    # differences above), and the bias of a channel that never fires gets none
+    demb = np.zeros(po.C)
+    demb[0] = 1.0
+    e, (_, _, _, v, nrm) = po.forward(p, codes, pooling="mean", rounding=False)
+    g = po.backward(p, codes, demb, pooling="mean", rounding=False)
+    o = po.TAPS * 4 * po.C + po.C + 2 * (po.TAPS * po.C * po.C + po.C) + po.TAPS * po.C * po.C
+    dv0 = (1.0 - e[0] * e[0]) / nrm
+    assert abs(g[o] - 2 / 14 * dv0) <= 1e-15, (g[o], 2 / 14 * dv0)
+    assert np.all(g[o + 1:o + po.C] == 0)
+    # the max pool routes the same gradient to one position only
+    gmax = po.backward(p, codes, demb, rounding=False)
+    _, (_, _, _, vm, nm) = po.forward(p, codes, rounding=False)
+    em0 = vm[0] / nm
+    assert abs(gmax[o] - (1.0 - em0 * em0) / nm) <= 1e-15
