@@ -287,6 +287,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_topk(TcArgs a) {
     //      columns 32 (w div 4) .. + 31 (16 reads): strand maximum, threshold, candidate buffers
     const int q = warp & 3, grp = warp >> 2, rbase = 16 * grp;
     const int frow = 32 * q + lane;  // fragment row of this thread in a tile
+    // the group's 16 thresholds as floats, kept in registers and reloaded only after a tile
+    // in which some warp of the group raised one (key 0, before the first compaction,
+    // accepts every score)
+    float th[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) th[i] = __int_as_float(0xff800000);
     for (int j = 0; j < nt; ++j) {
       const int s = j & 1;
       // every lane waits (acquire); the tensor-memory loads below need the whole warp
@@ -295,16 +301,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_topk(TcArgs a) {
       const int64_t f = (int64_t)(t0 + j) * kTcM + frow;
       if (ok) {
         tc_fence_after();
-        // the reads' thresholds as floats (key 0 accepts every score); rows past the last
-        // fragment take +inf and never pass.  Scores are made canonical (-0 -> +0), so on
-        // them the float order is the key order and "v > threshold" is "key > threshold key".
-        const bool fvalid = f < a.NF;
-        float th[16];
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const uint32_t k = s_theta[rbase + i];
-          th[i] = !fvalid ? __int_as_float(0x7f800000) : (k == 0u ? __int_as_float(0xff800000) : key_score(k));
-        }
+        // scores are made canonical (-0 -> +0), so on them the float order is the key order
+        // and "v > threshold" is "key > threshold key"; rows past the last fragment never pass
         uint32_t x[32];
         tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(s * kTcN + 2 * rbase), x);
         tmem_wait_ld();
@@ -315,25 +313,26 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_topk(TcArgs a) {
           v[i] = fmaxf(__uint_as_float(x[2 * i]), __uint_as_float(x[2 * i + 1])) + 0.0f;
           m |= (v[i] > th[i] ? 1u : 0u) << i;
         }
-        // append, read by read, only for the reads where some lane passes
-        uint32_t mm = __reduce_or_sync(0xffffffffu, m);
-        while (mm) {
-          const int i = __ffs(mm) - 1;
-          mm &= mm - 1u;
-          const int r = rbase + i;
-          const bool pred = (m >> i) & 1u;
-          const uint32_t b = __ballot_sync(0xffffffffu, pred);
-          const int leader = __ffs(b) - 1;
-          int basepos = 0;
-          if (lane == leader) basepos = atomicAdd(&s_cnt[r], __popc(b));
-          basepos = __shfl_sync(0xffffffffu, basepos, leader);
-          if (pred) {
-            float vi = v[0];
+        if (f >= a.NF) m = 0u;
+        // append, for the reads where some lane passes (a warp-uniform test per read)
+        const uint32_t mm = __reduce_or_sync(0xffffffffu, m);
+        if (mm) {
 #pragma unroll
-            for (int k = 1; k < 16; ++k) vi = (k == i) ? v[k] : vi;
-            const int pos = basepos + __popc(b & ((1u << lane) - 1u));
-            s_key[r * kTcCap + pos] = score_key(vi);
-            s_frag[r * kTcCap + pos] = (int32_t)f;
+          for (int i = 0; i < 16; ++i) {
+            if (mm & (1u << i)) {
+              const int r = rbase + i;
+              const bool pred = (m >> i) & 1u;
+              const uint32_t b = __ballot_sync(0xffffffffu, pred);
+              const int leader = __ffs(b) - 1;
+              int basepos = 0;
+              if (lane == leader) basepos = atomicAdd(&s_cnt[r], __popc(b));
+              basepos = __shfl_sync(0xffffffffu, basepos, leader);
+              if (pred) {
+                const int pos = basepos + __popc(b & ((1u << lane) - 1u));
+                s_key[r * kTcCap + pos] = score_key(v[i]);
+                s_frag[r * kTcCap + pos] = (int32_t)f;
+              }
+            }
           }
         }
       }
@@ -342,14 +341,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_topk(TcArgs a) {
       if (lane == 0) mbar_arrive(&tmem_free[s]);
       // every append of the group's reads for this tile is done
       const bool abort = grp_bar_or(grp, *s_abort != 0);
+      bool raised = false;
       if (!abort)
         for (int r = rbase + q; r < rbase + 16; r += 4)
           if (s_cnt[r] > kTcCap - kTcM) {
             s_theta[r] = warp_select(s_key + r * kTcCap, s_frag + r * kTcCap, s_cnt[r], a.K, lane);
             if (lane == 0) s_cnt[r] = a.K;
             __syncwarp();
+            raised = true;
           }
-      grp_bar(grp);  // the group's buffers compacted before its next appends
+      // the group's buffers compacted before its next appends; new thresholds are visible
+      if (grp_bar_or(grp, raised)) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const uint32_t k = s_theta[rbase + i];
+          th[i] = k == 0u ? __int_as_float(0xff800000) : key_score(k);
+        }
+      }
       if (abort) break;
     }
     // the K best of every read of the group (its buffers are final after the last group barrier)
