@@ -3,23 +3,27 @@
 // in[p + t - 3][ci] * w[t][ci][co], then bias + ReLU + length mask (forward) or the previous
 // layer's ReLU mask (backward-data, with flipped transposed weights).
 //
-// Persistent, warp-specialised kernel, one CTA per SM.  A CTA owns one half of the output
-// channels (64) for the whole launch: the 7 taps of that half (112 KB of B operands) are
-// copied into shared memory once and stay there.  Work item = 128 positions of one sequence;
-// even CTAs take the low half and odd CTAs the high half of the same items, so the partner's
-// read of an input tile hits L2.  Roles, linked only by mbarriers:
+// The GEMM per item (128 positions of one sequence) is D[co][p] = sum_t W_t[co][:] . X[p+t][:]
+// with M = 128 output channels, N = 128 positions, K = 7 taps x 128 input channels, so that
+// every MMA has N = 128, where the tensor cores run at their full rate (an MMA of N = 64 runs
+// at about 0.7 of it, whether its A operand comes from shared or tensor memory).  The weights
+// are the A operand and stay resident for the whole launch: taps 0-5 in tensor memory
+// (64 columns per tap: output channel = lane, two input channels per 32-bit column), tap 6 in
+// shared memory; the remaining 128 tensor-memory columns hold the accumulator.
+//
+// Persistent, warp-specialised kernel, one CTA per SM, items strided over the CTAs.  Roles,
+// linked only by mbarriers:
 //   warp 0  producer: per item two TMA tensor copies (channels 0-63 and 64-127, 134 rows of
-//           128 B each) into a three-stage ring of input tiles;
-//   warp 1  one thread issues the item's 56 MMAs (7 taps x 8 K-steps of M = 128, N = 64,
-//           K = 16, BF16 -> FP32) into one of three 64-column tensor-memory accumulators;
-//   warps 2-5  epilogue: tcgen05.ld of the accumulator (warp w reads lanes 32 (w mod 4) .. + 31),
-//           release it, then bias + ReLU + mask and the BF16 store.
+//           128 B each) into a four-stage ring of input tiles;
+//   warp 1  one thread issues the item's 56 MMAs (taps 0-5 with A from tensor memory, tap 6
+//           with A from shared memory; 8 K-steps of 16 each) into the accumulator;
+//   warps 2-5  epilogue: warp w owns output channels 32 (w mod 4) .. + 31 (its tensor-memory
+//           lane quarter); it reads the whole accumulator (thread = channel, 128 positions),
+//           releases it, then applies bias + ReLU + mask and stores BF16.
 // Each half of an input tile is K-major in the 128-byte swizzled layout (rows of 128 B in
 // 1 KB atoms of 8 rows, written swizzled by the TMA unit), so a K-step is a 32-byte start
 // offset inside a row and the tap shift is a start offset of t rows (t * 128 B); one staged
-// tile serves all 7 taps.  The resident weights use the
-// canonical K-major layout without swizzling.  Every wait is time-bounded and reports through
-// the error word.
+// tile serves all 7 taps.  Every wait is time-bounded and reports through the error word.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -37,27 +41,53 @@ namespace mss {
 
 namespace {
 
-constexpr int kCtM = 128;                              // positions per item
-constexpr int kCtN = 64;                               // output channels per CTA
+constexpr int kCtM = 128;                              // positions per item (the MMA's N)
 constexpr int kCtRows = kCtM + 6;                      // with the halo
-constexpr int kCtStages = 3;
+constexpr int kCtStages = 4;
 constexpr uint32_t kCtHalfA = 17 * 1024;               // 64 channels x 134 rows of 128 B, whole 1 KB atoms
 constexpr uint32_t kCtBytesA = 2 * kCtHalfA;           // 34,816 per stage
 constexpr uint32_t kCtTxA = 16 * kCtRows * 16;         // 34,304 bytes land per item
-constexpr uint32_t kCtGroupW = kCtN * 16;              // one channel group of a tap's half weights
-constexpr uint32_t kCtTapW = 16 * kCtGroupW;           // 16,384 per tap and half
-constexpr uint32_t kCtHalfW = kPropTaps * kCtTapW;     // 114,688 per half
-constexpr uint32_t kCtOffW = kCtStages * kCtBytesA;
-constexpr uint32_t kCtOffBar = kCtOffW + kCtHalfW;
+constexpr int kCtTmemTaps = 6;                         // taps whose weights live in tensor memory
+constexpr uint32_t kCtTapCols = kPropC / 2;            // 64 columns per tap (two BF16 per column)
+constexpr uint32_t kCtDCol = kCtTmemTaps * kCtTapCols; // 384: the accumulator's first column
+constexpr uint32_t kCtTmemCols = 512;
+constexpr uint32_t kCtTmemWBytes = kCtTmemTaps * kCtTapCols * kPropC * 4;  // 196,608
+constexpr uint32_t kCtW6Bytes = kPropC * kPropC * 2;  // tap 6, canonical K-major: 32,768
+constexpr uint32_t kCtOffW6 = kCtStages * kCtBytesA;
+constexpr uint32_t kCtOffBar = kCtOffW6 + kCtW6Bytes;
 constexpr uint32_t kCtSmem = kCtOffBar + 128;
 constexpr int kCtThreads = 192;
-constexpr uint32_t kCtTmemCols = 256;                  // power of two >= kCtStages * kCtN
-constexpr uint32_t kCtIdesc = idesc_bf16_f32(kCtM, kCtN);
+constexpr uint32_t kCtIdesc = idesc_bf16_f32(kPropC, kCtM);
 constexpr uint64_t kCtWaitNs = 2000000000ull;
 static_assert(kCtSmem + 1024 <= 227 * 1024, "shared memory of the conv CTA");
-static_assert(kCtStages * kCtN <= (int)kCtTmemCols, "tensor-memory columns");
-static_assert(kCtOffW % 1024 == 0 && kCtHalfA % 1024 == 0 && kCtBytesA % 1024 == 0, "operand alignment");
+static_assert(kCtDCol + kCtM <= kCtTmemCols, "tensor-memory columns");
+static_assert(kCtOffW6 % 1024 == 0 && kCtHalfA % 1024 == 0 && kCtBytesA % 1024 == 0, "operand alignment");
 static_assert(kCtRows * 128 <= (int)kCtHalfA, "input tile half");
+
+// D[tmem] (+)= A[tmem] * B[smem]^T (A: M lanes x 16 BF16, two per 32-bit column), one thread
+__device__ __forceinline__ void tc_mma_bf16_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                               uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// 32 consecutive 32-bit columns of this warp's 32 tensor-memory lanes (thread i -> lane i)
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+      "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, "
+      "%17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+      "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]),
+      "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]),
+      "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // Shared-memory descriptor of a K-major operand in the 128-byte swizzled layout (rows of 128 B,
 // 8-row atoms of 1 KB, the 16-byte chunks of row r XOR-ed with r mod 8, as the TMA unit writes
@@ -100,7 +130,7 @@ __device__ __forceinline__ ConvItem conv_item(int j, int ntile, const int32_t* l
 }
 
 __global__ void __launch_bounds__(kCtThreads, 1) k_conv_tc(const __grid_constant__ CUtensorMap tin,
-                                                           const uint8_t* __restrict__ wcanon,
+                                                           const uint8_t* __restrict__ wprep,
                                                            const float* __restrict__ bias,
                                                            const __nv_bfloat16* __restrict__ prev,
                                                            const int32_t* __restrict__ lens,
@@ -110,23 +140,24 @@ __global__ void __launch_bounds__(kCtThreads, 1) k_conv_tc(const __grid_constant
   __shared__ uint32_t s_tmem;
   __shared__ int32_t s_live[kCtStages];  // producer -> MMA issuer: the stage's item has live positions
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int half = blockIdx.x & 1, stride = gridDim.x >> 1;
-  const int first = blockIdx.x >> 1;
+  const int first = blockIdx.x, stride = gridDim.x;
   const int count = first < items ? (items - 1 - first) / stride + 1 : 0;
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + kCtOffBar);
-  uint64_t* wfull = bar;                       // the resident weights have landed
-  uint64_t* afull = bar + 1;                   // [kCtStages] input tile of the stage landed
-  uint64_t* done = bar + 1 + kCtStages;        // [kCtStages] MMAs of the stage's item completed
-  uint64_t* accfree = bar + 1 + 2 * kCtStages; // [kCtStages] epilogue has read the accumulator
+  uint64_t* wfull = bar;                        // tap 6's weights have landed
+  uint64_t* afull = bar + 1;                    // [kCtStages] input tile of the stage landed
+  uint64_t* afree = bar + 1 + kCtStages;        // [kCtStages] MMAs reading the stage completed
+  uint64_t* dfull = bar + 1 + 2 * kCtStages;    // the item's accumulator is complete
+  uint64_t* dfree = bar + 2 + 2 * kCtStages;    // the epilogue has read the accumulator
   const uint32_t sA = smem_u32(sm);
-  const uint32_t sW = sA + kCtOffW;
+  const uint32_t sW6 = sA + kCtOffW6;
   if (tid == 0) {
     mbar_init(wfull, 1);
     for (int s = 0; s < kCtStages; ++s) {
       mbar_init(&afull[s], 1);
-      mbar_init(&done[s], 1);
-      mbar_init(&accfree[s], 4);
+      mbar_init(&afree[s], 1);
     }
+    mbar_init(dfull, 1);
+    mbar_init(dfree, 4);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -137,18 +168,35 @@ __global__ void __launch_bounds__(kCtThreads, 1) k_conv_tc(const __grid_constant
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = s_tmem;
+  if (warp >= 2) {
+    // taps 0-5 of the weights into tensor memory: thread = output channel (its lane), tap t at
+    // columns 64 t .. 64 t + 63; the prepared words are [t][column][channel], so a warp's loads
+    // are contiguous
+    const int co = 32 * (warp & 3) + lane;
+    const uint32_t* wt = reinterpret_cast<const uint32_t*>(wprep);
+    for (int t = 0; t < kCtTmemTaps; ++t)
+#pragma unroll
+      for (int c0 = 0; c0 < (int)kCtTapCols; c0 += 32) {
+        uint32_t r[32];
+#pragma unroll
+        for (int c = 0; c < 32; ++c) r[c] = wt[((size_t)t * kCtTapCols + c0 + c) * kPropC + co];
+        tmem_st32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(t * kCtTapCols + c0), r);
+      }
+    tmem_wait_st();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
 
   if (warp == 0) {
     if (lane == 0 && count > 0) {  // producer
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tin)) : "memory");
-      mbar_arrive_expect_tx(wfull, kCtHalfW);
-      for (int t = 0; t < kPropTaps; ++t)
-        tma_load_1d(sm + kCtOffW + t * kCtTapW, wcanon + (size_t)half * kCtHalfW + (size_t)t * kCtTapW, kCtTapW,
-                    wfull);
+      mbar_arrive_expect_tx(wfull, kCtW6Bytes);
+      tma_load_1d(sm + kCtOffW6, wprep + kCtTmemWBytes, kCtW6Bytes, wfull);
       bool ok = true;
       for (int k = 0; k < count; ++k) {
         const int s = k % kCtStages, u = k / kCtStages;
-        if (k >= kCtStages && ok && !mbar_wait(&done[s], (uint32_t)((u - 1) & 1), kCtWaitNs)) {
+        if (k >= kCtStages && ok && !mbar_wait(&afree[s], (uint32_t)((u - 1) & 1), kCtWaitNs)) {
           ok = false;
           atomicOr(err, ERR_TIMEOUT);
         }
@@ -168,84 +216,70 @@ __global__ void __launch_bounds__(kCtThreads, 1) k_conv_tc(const __grid_constant
     if (lane == 0 && count > 0) {  // MMA issuer
       bool wok = mbar_wait(wfull, 0, kCtWaitNs);
       if (!wok) atomicOr(err, ERR_TIMEOUT);
+      const uint32_t d = tmem + kCtDCol;
       for (int k = 0; k < count; ++k) {
         const int s = k % kCtStages, u = k / kCtStages;
         bool go = mbar_wait(&afull[s], (uint32_t)(u & 1), kCtWaitNs);
-        if (go && k >= kCtStages) go = mbar_wait(&accfree[s], (uint32_t)((u - 1) & 1), kCtWaitNs);
+        if (go && k >= 1) go = mbar_wait(dfree, (uint32_t)((k - 1) & 1), kCtWaitNs);
         if (!go) atomicOr(err, ERR_TIMEOUT);
         tc_fence_after();
         if (wok && go && s_live[s]) {
-          const uint32_t a0 = sA + s * kCtBytesA, d = tmem + (uint32_t)(s * kCtN);
+          const uint32_t a0 = sA + s * kCtBytesA;
 #pragma unroll 1
-          for (int t = 0; t < kPropTaps; ++t) {
+          for (int t = 0; t < kCtTmemTaps; ++t) {
 #pragma unroll
             for (int ks = 0; ks < kPropC / 16; ++ks)
-              tc_mma_bf16(d, smem_desc_sw128(a0 + (ks >> 2) * kCtHalfA + t * 128 + (ks & 3) * 32),
-                          smem_desc(sW + t * kCtTapW + (2 * ks) * kCtGroupW, kCtGroupW, 128), kCtIdesc,
-                          (t > 0 || ks > 0) ? 1u : 0u);
+              tc_mma_bf16_ts(d, tmem + (uint32_t)(t * kCtTapCols + ks * 8),
+                             smem_desc_sw128(a0 + (ks >> 2) * kCtHalfA + t * 128 + (ks & 3) * 32), kCtIdesc,
+                             (t > 0 || ks > 0) ? 1u : 0u);
           }
-          tc_commit(&done[s]);
+#pragma unroll
+          for (int ks = 0; ks < kPropC / 16; ++ks)
+            tc_mma_bf16(d, smem_desc(sW6 + ks * 256, kCanonLbo, kCanonSbo),
+                        smem_desc_sw128(a0 + (ks >> 2) * kCtHalfA + kCtTmemTaps * 128 + (ks & 3) * 32), kCtIdesc,
+                        1u);
+          tc_commit(&afree[s]);
+          tc_commit(dfull);
         } else {
-          mbar_arrive(&done[s]);
+          mbar_arrive(&afree[s]);
+          mbar_arrive(dfull);
         }
       }
     }
-  } else {  // epilogue: thread = position p0 + 32 (warp mod 4) + lane, the CTA's 64 channels
-    const int q = warp & 3;
+  } else {  // epilogue: thread = output channel 32 (warp mod 4) + lane, the item's 128 positions
+    const int q = warp & 3, co = 32 * q + lane;
+    const float b_co = mode == 0 ? bias[co] : 0.f;
     for (int k = 0; k < count; ++k) {
-      const int s = k % kCtStages, u = k / kCtStages;
-      const bool ok = mbar_wait(&done[s], (uint32_t)(u & 1), kCtWaitNs);
+      const bool ok = mbar_wait(dfull, (uint32_t)(k & 1), kCtWaitNs);
       if (!ok && lane == 0) atomicOr(err, ERR_TIMEOUT);
       __syncwarp();
       tc_fence_after();
-      uint32_t x[2][32];
-      const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(s * kCtN);
-      tmem_ld32(ta, x[0]);
-      tmem_ld32(ta + 32, x[1]);
+      uint32_t x[4][32];
+      const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + kCtDCol;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) tmem_ld32(ta + 32 * c, x[c]);
       tmem_wait_ld();
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(&accfree[s]);
+      if (lane == 0) mbar_arrive(dfree);
       const ConvItem it = conv_item(first + k * stride, ntile, lens);
-      const int p = it.p0 + 32 * q + lane;
-      const bool valid = ok && it.live && p < lens[it.n];
+      const int len = lens[it.n];
+      const int64_t base = ((int64_t)it.n * rows + it.p0 + 3) * kPropC + co;
 #pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        const int ch = half * kCtN + 32 * c;
-        const int64_t orow = ((int64_t)it.n * rows + p + 3) * kPropC + ch;
-        uint32_t packed[16];
-        if (mode == 0) {
+      for (int c = 0; c < 4; ++c)
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            float v0 = fmaxf(__uint_as_float(x[c][2 * j]) + bias[ch + 2 * j], 0.f);
-            float v1 = fmaxf(__uint_as_float(x[c][2 * j + 1]) + bias[ch + 2 * j + 1], 0.f);
-            if (!valid) v0 = v1 = 0.f;
-            __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
-            packed[j] = *reinterpret_cast<uint32_t*>(&h);
+        for (int j = 0; j < 32; ++j) {
+          const int p = it.p0 + 32 * c + j;
+          const int64_t o = base + (int64_t)(32 * c + j) * kPropC;
+          float v = __uint_as_float(x[c][j]);
+          if (mode == 0) {
+            v = fmaxf(v + b_co, 0.f);
+          } else if (!(ok && it.live && p < len && __bfloat162float(prev[o]) > 0.f)) {
+            v = 0.f;
           }
-        } else {
-          const uint4* pv = reinterpret_cast<const uint4*>(prev + orow);
-#pragma unroll
-          for (int v = 0; v < 4; ++v) {
-            const uint4 m4 = valid ? pv[v] : make_uint4(0, 0, 0, 0);
-            const uint32_t mw[4] = {m4.x, m4.y, m4.z, m4.w};
-#pragma unroll
-            for (int h2 = 0; h2 < 4; ++h2) {
-              const int j = 4 * v + h2;
-              const __nv_bfloat162 pm = *reinterpret_cast<const __nv_bfloat162*>(&mw[h2]);
-              float v0 = __uint_as_float(x[c][2 * j]), v1 = __uint_as_float(x[c][2 * j + 1]);
-              if (!(__bfloat162float(pm.x) > 0.f)) v0 = 0.f;
-              if (!(__bfloat162float(pm.y) > 0.f)) v1 = 0.f;
-              __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
-              packed[j] = *reinterpret_cast<uint32_t*>(&h);
-            }
-          }
+          if (!(ok && it.live && p < len)) v = 0.f;
+          out[o] = __float2bfloat16_rn(v);
         }
-        uint4* dst = reinterpret_cast<uint4*>(out + orow);
-#pragma unroll
-        for (int v = 0; v < 4; ++v)
-          dst[v] = make_uint4(packed[4 * v], packed[4 * v + 1], packed[4 * v + 2], packed[4 * v + 3]);
-      }
     }
   }
   tc_fence_before();
@@ -257,25 +291,33 @@ __global__ void __launch_bounds__(kCtThreads, 1) k_conv_tc(const __grid_constant
   }
 }
 
-// w[t][in][out] (bf16) -> per output half h and tap t the B operand B[out][in] in the
-// k-group-major layout: byte h * 114688 + t * 16384 + (in / 8) * 1024 + (out % 64) * 16 + (in % 8) * 2
+// w[t][in][out] (bf16) -> the kernel's resident A operands: for taps 0-5 the tensor-memory
+// words [t][column c][out] = (w[t][2c][out], w[t][2c + 1][out]) (low half first), then tap 6
+// as a [out][in] K-major tile in the canonical layout without swizzling.  One thread per
+// (tap, column, output channel).
 __global__ void k_canon_weights(const __nv_bfloat16* __restrict__ w, uint8_t* __restrict__ dst) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;  // one thread per (t, out, group of 8 inputs)
-  if (e >= kPropTaps * 128 * 16) return;
-  const int t = e / (128 * 16), rem = e - t * 128 * 16, o = rem >> 4, g = rem & 15;
-  __align__(16) __nv_bfloat16 v[8];
-#pragma unroll
-  for (int i = 0; i < 8; ++i) v[i] = w[((int64_t)t * 128 + g * 8 + i) * 128 + o];
-  *reinterpret_cast<uint4*>(dst + (size_t)(o / kCtN) * kCtHalfW + (size_t)t * kCtTapW + g * kCtGroupW +
-                            (o % kCtN) * 16) = *reinterpret_cast<uint4*>(v);
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= kPropTaps * (int)kCtTapCols * kPropC) return;
+  const int t = e / ((int)kCtTapCols * kPropC), rem = e - t * (int)kCtTapCols * kPropC;
+  const int c = rem / kPropC, o = rem - c * kPropC;
+  const __nv_bfloat16 lo = w[((int64_t)t * kPropC + 2 * c) * kPropC + o];
+  const __nv_bfloat16 hi = w[((int64_t)t * kPropC + 2 * c + 1) * kPropC + o];
+  if (t < kCtTmemTaps) {
+    reinterpret_cast<uint32_t*>(dst)[e] =
+        (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+  } else {
+    __nv_bfloat16* w6 = reinterpret_cast<__nv_bfloat16*>(dst + kCtTmemWBytes);
+    w6[canon_offset((uint32_t)o, (uint32_t)(2 * c)) / 2] = lo;
+    w6[canon_offset((uint32_t)o, (uint32_t)(2 * c + 1)) / 2] = hi;
+  }
 }
 
 }  // namespace
 
-int64_t prop_canon_weight_bytes() { return (int64_t)(kPropC / kCtN) * kCtHalfW; }
+int64_t prop_canon_weight_bytes() { return (int64_t)kCtTmemWBytes + kCtW6Bytes; }
 
 cudaError_t prop_canon_weights(const __nv_bfloat16* w, void* dst, cudaStream_t s) {
-  const int n = kPropTaps * 128 * 16;
+  const int n = kPropTaps * (int)kCtTapCols * kPropC;
   k_canon_weights<<<(n + 255) / 256, 256, 0, s>>>(w, static_cast<uint8_t*>(dst));
   return cudaGetLastError();
 }
@@ -324,8 +366,8 @@ cudaError_t prop_conv_tc(const __nv_bfloat16* in, const void* wcanon, const floa
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return cudaErrorInvalidValue;
-  // one CTA per SM, an even count (the two output halves of an item go to CTAs 2i and 2i + 1)
-  const int64_t grid = std::min<int64_t>(std::max(2, sms & ~1), 2 * items);
+  // one CTA per SM (the tensor memory holds one CTA's weights and accumulator)
+  const int64_t grid = std::min<int64_t>(std::max(1, sms), items);
   k_conv_tc<<<(unsigned)grid, kCtThreads, kCtSmem, s>>>(map, static_cast<const uint8_t*>(wcanon), bias, prev, lens,
                                                          out, rows, ntile, (int32_t)items, mode, err);
   return cudaGetLastError();
