@@ -14,12 +14,15 @@
 // Persistent, warp-specialised kernel, one CTA per SM, items strided over the CTAs.  Roles,
 // linked only by mbarriers:
 //   warp 0  producer: per item two TMA tensor copies (channels 0-63 and 64-127, 134 rows of
-//           128 B each) into a four-stage ring of input tiles;
+//           128 B each) into a three-stage ring of input tiles, and in the backward pass one
+//           more (the previous layer's activations at the item's 128 positions, whose sign is
+//           the ReLU mask) into a two-slot ring;
 //   warp 1  one thread issues the item's 56 MMAs (taps 0-5 with A from tensor memory, tap 6
 //           with A from shared memory; 8 K-steps of 16 each) into the accumulator;
 //   warps 2-5  epilogue: warp w owns output channels 32 (w mod 4) .. + 31 (its tensor-memory
 //           lane quarter); it reads the whole accumulator (thread = channel, 128 positions),
-//           releases it, then applies bias + ReLU + mask and stores BF16.
+//           releases it, then applies bias + ReLU + length mask (forward) or the ReLU mask
+//           staged by the producer (backward) and stores BF16.
 // Each half of an input tile is K-major in the 128-byte swizzled layout (rows of 128 B in
 // 1 KB atoms of 8 rows, written swizzled by the TMA unit), so a K-step is a 32-byte start
 // offset inside a row and the tap shift is a start offset of t rows (t * 128 B); one staged
@@ -43,7 +46,7 @@ namespace {
 
 constexpr int kCtM = 128;                              // positions per item (the MMA's N)
 constexpr int kCtRows = kCtM + 6;                      // with the halo
-constexpr int kCtStages = 4;
+constexpr int kCtStages = 3;
 constexpr uint32_t kCtHalfA = 17 * 1024;               // 64 channels x 134 rows of 128 B, whole 1 KB atoms
 constexpr uint32_t kCtBytesA = 2 * kCtHalfA;           // 34,816 per stage
 constexpr uint32_t kCtTxA = 16 * kCtRows * 16;         // 34,304 bytes land per item
@@ -54,14 +57,18 @@ constexpr uint32_t kCtTmemCols = 512;
 constexpr uint32_t kCtTmemWBytes = kCtTmemTaps * kCtTapCols * kPropC * 4;  // 196,608
 constexpr uint32_t kCtW6Bytes = kPropC * kPropC * 2;  // tap 6, canonical K-major: 32,768
 constexpr uint32_t kCtOffW6 = kCtStages * kCtBytesA;
-constexpr uint32_t kCtOffBar = kCtOffW6 + kCtW6Bytes;
+constexpr int kCtMaskSlots = 2;
+constexpr uint32_t kCtMaskBytes = kCtM * kPropC * 2;    // 128 rows of 256 B, no swizzle
+constexpr uint32_t kCtOffMask = kCtOffW6 + kCtW6Bytes;
+constexpr uint32_t kCtOffBar = kCtOffMask + kCtMaskSlots * kCtMaskBytes;
 constexpr uint32_t kCtSmem = kCtOffBar + 128;
 constexpr int kCtThreads = 192;
 constexpr uint32_t kCtIdesc = idesc_bf16_f32(kPropC, kCtM);
 constexpr uint64_t kCtWaitNs = 2000000000ull;
 static_assert(kCtSmem + 1024 <= 227 * 1024, "shared memory of the conv CTA");
 static_assert(kCtDCol + kCtM <= kCtTmemCols, "tensor-memory columns");
-static_assert(kCtOffW6 % 1024 == 0 && kCtHalfA % 1024 == 0 && kCtBytesA % 1024 == 0, "operand alignment");
+static_assert(kCtOffW6 % 1024 == 0 && kCtHalfA % 1024 == 0 && kCtBytesA % 1024 == 0 && kCtOffMask % 1024 == 0,
+              "operand alignment");
 static_assert(kCtRows * 128 <= (int)kCtHalfA, "input tile half");
 
 // D[tmem] (+)= A[tmem] * B[smem]^T (A: M lanes x 16 BF16, two per 32-bit column), one thread
@@ -130,9 +137,9 @@ __device__ __forceinline__ ConvItem conv_item(int j, int ntile, const int32_t* l
 }
 
 __global__ void __launch_bounds__(kCtThreads, 1) k_conv_tc(const __grid_constant__ CUtensorMap tin,
+                                                           const __grid_constant__ CUtensorMap tprev,
                                                            const uint8_t* __restrict__ wprep,
                                                            const float* __restrict__ bias,
-                                                           const __nv_bfloat16* __restrict__ prev,
                                                            const int32_t* __restrict__ lens,
                                                            __nv_bfloat16* __restrict__ out, int32_t rows,
                                                            int32_t ntile, int32_t items, int mode, int32_t* err) {
@@ -148,6 +155,8 @@ __global__ void __launch_bounds__(kCtThreads, 1) k_conv_tc(const __grid_constant
   uint64_t* afree = bar + 1 + kCtStages;        // [kCtStages] MMAs reading the stage completed
   uint64_t* dfull = bar + 1 + 2 * kCtStages;    // the item's accumulator is complete
   uint64_t* dfree = bar + 2 + 2 * kCtStages;    // the epilogue has read the accumulator
+  uint64_t* mfull = bar + 3 + 2 * kCtStages;    // [kCtMaskSlots] backward: the item's mask tile landed
+  uint64_t* mfree = bar + 3 + 2 * kCtStages + kCtMaskSlots;  // [kCtMaskSlots] the epilogue is done with it
   const uint32_t sA = smem_u32(sm);
   const uint32_t sW6 = sA + kCtOffW6;
   if (tid == 0) {
@@ -158,6 +167,10 @@ __global__ void __launch_bounds__(kCtThreads, 1) k_conv_tc(const __grid_constant
     }
     mbar_init(dfull, 1);
     mbar_init(dfree, 4);
+    for (int m = 0; m < kCtMaskSlots; ++m) {
+      mbar_init(&mfull[m], 1);
+      mbar_init(&mfree[m], 4);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -191,6 +204,7 @@ __global__ void __launch_bounds__(kCtThreads, 1) k_conv_tc(const __grid_constant
   if (warp == 0) {
     if (lane == 0 && count > 0) {  // producer
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tin)) : "memory");
+      if (mode == 1) asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tprev)) : "memory");
       mbar_arrive_expect_tx(wfull, kCtW6Bytes);
       tma_load_1d(sm + kCtOffW6, wprep + kCtTmemWBytes, kCtW6Bytes, wfull);
       bool ok = true;
@@ -202,13 +216,26 @@ __global__ void __launch_bounds__(kCtThreads, 1) k_conv_tc(const __grid_constant
         }
         const ConvItem it = conv_item(first + k * stride, ntile, lens);
         s_live[s] = ok && it.live;  // published by the arrive below (release), read after the wait
+        const int32_t y = it.n * rows + it.p0;  // padded row of position p0 - 3
         if (ok && it.live) {
           mbar_arrive_expect_tx(&afull[s], kCtTxA);
-          const int32_t y = it.n * rows + it.p0;  // padded row of position p0 - 3
 #pragma unroll
           for (int h = 0; h < 2; ++h) tma_load_2d(sA + s * kCtBytesA + h * kCtHalfA, &tin, 64 * h, y, &afull[s]);
         } else {
           mbar_arrive(&afull[s]);
+        }
+        if (mode == 1) {  // the mask tile of the item: rows of positions p0 .. p0 + 127
+          const int m = k % kCtMaskSlots, v = k / kCtMaskSlots;
+          if (k >= kCtMaskSlots && ok && !mbar_wait(&mfree[m], (uint32_t)((v - 1) & 1), kCtWaitNs)) {
+            ok = false;
+            atomicOr(err, ERR_TIMEOUT);
+          }
+          if (ok && it.live) {
+            mbar_arrive_expect_tx(&mfull[m], kCtMaskBytes);
+            tma_load_2d(sA + kCtOffMask + m * kCtMaskBytes, &tprev, 0, y + 3, &mfull[m]);
+          } else {
+            mbar_arrive(&mfull[m]);
+          }
         }
       }
     }
@@ -265,21 +292,32 @@ __global__ void __launch_bounds__(kCtThreads, 1) k_conv_tc(const __grid_constant
       const ConvItem it = conv_item(first + k * stride, ntile, lens);
       const int len = lens[it.n];
       const int64_t base = ((int64_t)it.n * rows + it.p0 + 3) * kPropC + co;
+      const int m = k % kCtMaskSlots;
+      bool mok = true;
+      if (mode == 1) {
+        mok = __all_sync(0xffffffffu, mbar_wait(&mfull[m], (uint32_t)((k / kCtMaskSlots) & 1), kCtWaitNs));
+        if (!mok && lane == 0) atomicOr(err, ERR_TIMEOUT);
+      }
+      const __nv_bfloat16* mk = reinterpret_cast<const __nv_bfloat16*>(sm + kCtOffMask + m * kCtMaskBytes) + co;
 #pragma unroll
       for (int c = 0; c < 4; ++c)
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const int p = it.p0 + 32 * c + j;
           const int64_t o = base + (int64_t)(32 * c + j) * kPropC;
+          const bool valid = ok && mok && it.live && p < len;
           float v = __uint_as_float(x[c][j]);
-          if (mode == 0) {
+          if (mode == 0)
             v = fmaxf(v + b_co, 0.f);
-          } else if (!(ok && it.live && p < len && __bfloat162float(prev[o]) > 0.f)) {
+          else if (!(valid && __bfloat162float(mk[(32 * c + j) * kPropC]) > 0.f))
             v = 0.f;
-          }
-          if (!(ok && it.live && p < len)) v = 0.f;
+          if (!valid) v = 0.f;
           out[o] = __float2bfloat16_rn(v);
         }
+      if (mode == 1) {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&mfree[m]);
+      }
     }
   }
   tc_fence_before();
@@ -366,9 +404,21 @@ cudaError_t prop_conv_tc(const __nv_bfloat16* in, const void* wcanon, const floa
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return cudaErrorInvalidValue;
+  // backward: the previous layer's activations, whose sign masks the gradient, as 128-row
+  // tiles of all 128 channels (256-byte rows, no swizzle); the forward pass passes the input
+  // map in its place (unused)
+  CUtensorMap pmap = map;
+  if (mode == 1) {
+    if (!prev || (reinterpret_cast<uintptr_t>(prev) & 15u) != 0) return cudaErrorInvalidValue;
+    const cuuint32_t pbox[2] = {(cuuint32_t)kPropC, (cuuint32_t)kCtM};
+    if (encode(&pmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(prev), dims, strides, pbox,
+               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
+  }
   // one CTA per SM (the tensor memory holds one CTA's weights and accumulator)
   const int64_t grid = std::min<int64_t>(std::max(1, sms), items);
-  k_conv_tc<<<(unsigned)grid, kCtThreads, kCtSmem, s>>>(map, static_cast<const uint8_t*>(wcanon), bias, prev, lens,
+  k_conv_tc<<<(unsigned)grid, kCtThreads, kCtSmem, s>>>(map, pmap, static_cast<const uint8_t*>(wcanon), bias, lens,
                                                          out, rows, ntile, (int32_t)items, mode, err);
   return cudaGetLastError();
 }
