@@ -373,6 +373,23 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
+cudaError_t prop_tensor_map_rows(CUtensorMap* map, const __nv_bfloat16* base, int64_t nrows, uint32_t box_ch,
+                                 uint32_t box_rows, bool swizzle128) {
+  // row coordinates of a tensor map are 32-bit; the base must be 16-byte aligned
+  if (nrows <= 0 || nrows > INT32_MAX || (reinterpret_cast<uintptr_t>(base) & 15u) != 0) return cudaErrorInvalidValue;
+  PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+  if (!encode) return cudaErrorNotSupported;
+  const cuuint64_t dims[2] = {(cuuint64_t)kPropC, (cuuint64_t)nrows};
+  const cuuint64_t strides[1] = {(cuuint64_t)kPropC * sizeof(__nv_bfloat16)};
+  const cuuint32_t box[2] = {box_ch, box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  if (encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(base), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
+  return cudaSuccess;
+}
+
 cudaError_t prop_conv_tc(const __nv_bfloat16* in, const void* wcanon, const float* bias, const __nv_bfloat16* prev,
                          const int32_t* lens, __nv_bfloat16* out, int32_t n, int32_t rows, int mode, int32_t* err,
                          cudaStream_t s) {
@@ -391,30 +408,17 @@ cudaError_t prop_conv_tc(const __nv_bfloat16* in, const void* wcanon, const floa
   const int32_t ntile = (rows - 6) / kCtM;
   const int64_t items = (int64_t)n * ntile;
   if (items <= 0) return cudaSuccess;
-  // row coordinates of the tensor map are 32-bit; the base must be 16-byte aligned
-  if ((int64_t)n * rows > INT32_MAX || (reinterpret_cast<uintptr_t>(in) & 15u) != 0) return cudaErrorInvalidValue;
-  PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
-  if (!encode) return cudaErrorNotSupported;
-  CUtensorMap map;
-  const cuuint64_t dims[2] = {(cuuint64_t)kPropC, (cuuint64_t)n * rows};
-  const cuuint64_t strides[1] = {(cuuint64_t)kPropC * sizeof(__nv_bfloat16)};
-  const cuuint32_t box[2] = {64, (cuuint32_t)kCtRows};
-  const cuuint32_t estr[2] = {1, 1};
-  if (encode(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(in), dims, strides, box, estr,
-             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-    return cudaErrorInvalidValue;
+  CUtensorMap map, pmap;
+  cudaError_t e = prop_tensor_map_rows(&map, in, (int64_t)n * rows, 64, (uint32_t)kCtRows, true);
+  if (e != cudaSuccess) return e;
   // backward: the previous layer's activations, whose sign masks the gradient, as 128-row
   // tiles of all 128 channels (256-byte rows, no swizzle); the forward pass passes the input
   // map in its place (unused)
-  CUtensorMap pmap = map;
+  pmap = map;
   if (mode == 1) {
-    if (!prev || (reinterpret_cast<uintptr_t>(prev) & 15u) != 0) return cudaErrorInvalidValue;
-    const cuuint32_t pbox[2] = {(cuuint32_t)kPropC, (cuuint32_t)kCtM};
-    if (encode(&pmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(prev), dims, strides, pbox,
-               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-      return cudaErrorInvalidValue;
+    if (!prev) return cudaErrorInvalidValue;
+    e = prop_tensor_map_rows(&pmap, prev, (int64_t)n * rows, (uint32_t)kPropC, (uint32_t)kCtM, false);
+    if (e != cudaSuccess) return e;
   }
   // one CTA per SM (the tensor memory holds one CTA's weights and accumulator)
   const int64_t grid = std::min<int64_t>(std::max(1, sms), items);

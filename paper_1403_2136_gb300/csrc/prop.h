@@ -1,5 +1,6 @@
 // Host-side declarations of the learned-proposal kernels (prop.cu); not part of the ABI.
 #pragma once
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -17,6 +18,12 @@ constexpr int64_t kPropParams = kPropW1 + kPropC + 3 * (kPropWl + kPropC);
 inline int64_t prop_off_b1() { return kPropW1; }
 inline int64_t prop_off_w(int layer) { return kPropW1 + kPropC + (int64_t)(layer - 2) * (kPropWl + kPropC); }
 inline int64_t prop_off_b(int layer) { return prop_off_w(layer) + kPropWl; }
+
+// 2-D TMA tensor map over an activation buffer of nrows rows x 128 BF16 channels, boxes of
+// box_ch channels x box_rows rows, 128-byte swizzle or none (conv_tc.cu).  cudaErrorInvalidValue
+// for a base that is not 16-byte aligned or more than 2^31 - 1 rows.
+cudaError_t prop_tensor_map_rows(CUtensorMap* map, const __nv_bfloat16* base, int64_t nrows, uint32_t box_ch,
+                                 uint32_t box_rows, bool swizzle128);
 
 // rows of an activation buffer for sequences of at most maxlen positions
 inline int32_t prop_rows(int32_t maxlen) { return ((maxlen + 127) / 128) * 128 + 6; }

@@ -7,15 +7,17 @@
 // Layout: activations and gradients are BF16 rows [sequence][position + 3][128 channels] (three
 // zero halo rows on either side), so a tile of positions is already "MN-major" for the MMA:
 // channels contiguous, positions strided.  A CTA owns a run of 128-position tiles and a group of
-// taps (0-3 or 4-6) whose FP32 accumulators (128 columns each) fill the tensor memory.  Per
-// tile its 128 threads copy, with 16-byte cp.async, the input rows of the tile's positions
-// shifted by the group's first tap (131 rows, padded to 136) and the 128 gradient rows into a
-// three-stage ring, two tiles ahead of the MMAs; each 16-byte chunk (8 channels of one row) lands at
-// channel-group * stride + row * 16, so that rows are 16 bytes apart throughout and a tap's
-// shift is a start-address offset of 16 bytes per row.  One thread issues, per tap, eight
-// tcgen05.mma (K = 16 positions each) and commits them on the stage's mbarrier; the next copy
-// into that stage waits for it.  At the end the four warps read their 32 accumulator
-// lanes (input channels) back and add them to dw with FP32 atomics.  Every wait is bounded.
+// taps (0-3 or 4-6) whose FP32 accumulators (128 columns each) fill the tensor memory.  One
+// thread stages each tile with TMA tensor copies into a three-stage ring, two tiles ahead of
+// the MMAs: 16 boxes of 8 channels x 131 input rows (the tile's positions shifted by the
+// group's first tap, plus the group's other tap shifts) and 16 boxes of 8 channels x 128
+// gradient rows; box c lands at c * stride, so that each 16-byte chunk (8 channels of one
+// row) sits at channel-group * stride + row * 16, rows are 16 bytes apart throughout, and a
+// tap's shift is a start-address offset of 16 bytes per row.  The same thread issues, per
+// tap, eight tcgen05.mma (K = 16 positions each) and commits them on the stage's mbarrier,
+// which the next copy into that stage waits for.  At the end the four warps read their 32
+// accumulator lanes (input channels) back and add them to dw with 16-byte FP32 atomics along
+// the output channels.  Every wait is bounded.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -34,14 +36,17 @@ constexpr int kWgThreads = 128;
 constexpr int kWgTile = 128;                              // positions per tile (MMA K total)
 constexpr int kWgTapsPerCta = 4;                          // 4 x 128 FP32 columns = all of TMEM
 constexpr int kWgARows = 136;                             // 128 + 3 tap shifts, padded to 8
+constexpr int kWgABox = 131;                              // rows copied: 128 + 3 tap shifts
 constexpr uint32_t kWgAStride = kWgARows * 16;            // bytes between 8-channel groups of A
 constexpr uint32_t kWgBStride = kWgTile * 16;             // the same for B
 constexpr uint32_t kWgABytes = 16 * kWgAStride;           // 34,816
 constexpr uint32_t kWgBBytes = 16 * kWgBStride;           // 32,768
 constexpr uint32_t kWgStage = kWgABytes + kWgBBytes;
+constexpr uint32_t kWgTx = 16 * (kWgABox + kWgTile) * 16; // bytes landing per tile
 constexpr int kWgStages = 3;                              // copies two tiles ahead
 constexpr uint32_t kWgSmem = kWgStages * kWgStage + 64;   // stages, mbarriers, TMEM slot
 constexpr uint64_t kWgWaitNs = 2000000000ull;
+static_assert(kWgAStride % 128 == 0 && kWgBStride % 128 == 0 && kWgStage % 128 == 0, "TMA destinations");
 // MN-major operands without swizzling: core matrices of 8 rows (K) x 16 bytes (8 MN
 // elements); the descriptor's leading offset is the distance between core matrices adjacent
 // in K (8 rows = 128 B here), its stride offset the distance between core matrices adjacent in
@@ -51,17 +56,25 @@ constexpr uint32_t kWgCoreK = 128;
 // instruction descriptor: BF16 x BF16 -> FP32, M = N = 128, A and B MN-major (bits 15, 16)
 constexpr uint32_t kWgIdesc = idesc_bf16_f32(128, 128) | (1u << 15) | (1u << 16);
 
-__device__ __forceinline__ void cp_async16_wg(uint32_t dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+// 2-D tiled TMA load (channel x, row y) completing on bar
+__device__ __forceinline__ void tma_tile_2d(uint32_t dst, const CUtensorMap* map, int32_t x, int32_t y,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+      "[%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
 }
 
 __global__ void __launch_bounds__(kWgThreads, 1)
-    k_conv_wgrad_tc(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ g,
+    k_conv_wgrad_tc(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tg,
                     const int32_t* __restrict__ lens, float* __restrict__ dw, int32_t n_seq, int32_t rows,
                     int32_t tiles_per_cta, int32_t* err) {
   extern __shared__ __align__(1024) uint8_t sm[];
-  uint64_t* done = reinterpret_cast<uint64_t*>(sm + kWgStages * kWgStage);   // [kWgStages]
-  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(sm + kWgStages * kWgStage + 8 * kWgStages);
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + kWgStages * kWgStage);       // [kWgStages]
+  uint64_t* done = full + kWgStages;                                              // [kWgStages]
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(done + kWgStages);
+  uint32_t* s_issued = s_tmem + 1;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int t0 = blockIdx.y * kWgTapsPerCta;
   const int ntaps = min(kWgTapsPerCta, kPropTaps - t0);
@@ -71,7 +84,10 @@ __global__ void __launch_bounds__(kWgThreads, 1)
   const int64_t last = min(total, first + tiles_per_cta);
 
   if (tid == 0) {
-    for (int k = 0; k < kWgStages; ++k) mbar_init(&done[k], 1);
+    for (int k = 0; k < kWgStages; ++k) {
+      mbar_init(&full[k], 1);
+      mbar_init(&done[k], 1);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -83,69 +99,52 @@ __global__ void __launch_bounds__(kWgThreads, 1)
   tc_fence_after();
   const uint32_t tmem = *s_tmem;
 
-  // tiles past a sequence's length carry zero gradients: skip them (the same for every thread)
-  auto next_live = [&](int64_t tile) {
-    while (tile < last) {
+  if (tid == 0) {
+    // tiles past a sequence's length carry zero gradients: skip them
+    auto next_live = [&](int64_t tile) {
+      while (tile < last) {
+        const int n = (int)(tile / tiles_per_seq);
+        if ((int)(tile - (int64_t)n * tiles_per_seq) * kWgTile < lens[n]) break;
+        ++tile;
+      }
+      return tile;
+    };
+    // live tile k goes to stage k mod kWgStages: input rows p0 + t0 .. + 130 (buffer rows; the
+    // rows past what this group's taps read are never multiplied) and gradient rows p0 + 3 ..
+    auto stage_copy = [&](int64_t tile, int s) {
       const int n = (int)(tile / tiles_per_seq);
-      if ((int)(tile - (int64_t)n * tiles_per_seq) * kWgTile < lens[n]) break;
-      ++tile;
-    }
-    return tile;
-  };
-  // copy tile `tile` into stage s: the input rows p0 + t0 + r (buffer rows: position
-  // p0 + t0 + r - 3), r < ntaps - 1 + 128 (the last tile's last row is the sequence's last buffer
-  // row; the pad rows up to 135 are never read by an MMA of a tap of this group), and the
-  // gradient rows of positions p0 .. p0 + 127 (buffer rows p0 + 3 ...)
-  auto stage_copy = [&](int64_t tile, int s) {
-    const int n = (int)(tile / tiles_per_seq);
-    const int p0 = (int)(tile - (int64_t)n * tiles_per_seq) * kWgTile;
-    const uint32_t sA = smem_u32(sm + s * kWgStage), sB = sA + kWgABytes;
-    const __nv_bfloat16* ia = in + ((int64_t)n * rows + p0 + t0) * kPropC;
-    const int arows = ntaps - 1 + kWgTile;
-    for (int e = tid; e < arows * 16; e += kWgThreads) {
-      const int r = e >> 4, c = e & 15;
-      cp_async16_wg(sA + c * kWgAStride + r * 16, ia + (int64_t)r * kPropC + c * 8);
-    }
-    const __nv_bfloat16* gb = g + ((int64_t)n * rows + p0 + 3) * kPropC;
-    for (int e = tid; e < kWgTile * 16; e += kWgThreads) {
-      const int r = e >> 4, c = e & 15;
-      cp_async16_wg(sB + c * kWgBStride + r * 16, gb + (int64_t)r * kPropC + c * 8);
-    }
-  };
-
-  // Live tile k goes to stage k mod kWgStages and its MMAs commit on done[k mod kWgStages].
-  // Every thread commits one cp.async group per prologue slot and per loop iteration (empty
-  // once the tiles run out), so that group k holds live tile k's copies.
-  bool ok = true;
-  int64_t fetch = next_live(first);  // the next live tile to copy
-  int copied = 0, issued = 0;         // live tiles copied / whose MMAs were issued
-  for (int k = 0; k < kWgStages - 1; ++k) {
-    if (fetch < last) {
+      const int p0 = (int)(tile - (int64_t)n * tiles_per_seq) * kWgTile;
+      const uint32_t sA = smem_u32(sm + s * kWgStage), sB = sA + kWgABytes;
+      mbar_arrive_expect_tx(&full[s], kWgTx);
+      const int32_t ya = n * rows + p0 + t0, yb = n * rows + p0 + 3;
+      for (int c = 0; c < 16; ++c) {
+        tma_tile_2d(sA + c * kWgAStride, &tin, 8 * c, ya, &full[s]);
+        tma_tile_2d(sB + c * kWgBStride, &tg, 8 * c, yb, &full[s]);
+      }
+    };
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tin)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tg)) : "memory");
+    bool ok = true;
+    int64_t fetch = next_live(first);
+    int copied = 0, issued = 0;
+    for (int k = 0; k < kWgStages - 1 && fetch < last; ++k) {
       stage_copy(fetch, k);
       fetch = next_live(fetch + 1);
       ++copied;
     }
-    asm volatile("cp.async.commit_group;" ::: "memory");
-  }
-  while (issued < copied) {
-    const int s = issued % kWgStages;
-    if (fetch < last) {
-      // copied == issued + kWgStages - 1: the stage to refill was last read by tile issued - 1
-      if (issued >= 1)
-        ok = mbar_wait(&done[(issued - 1) % kWgStages], (uint32_t)(((issued - 1) / kWgStages) & 1), kWgWaitNs);
-      if (!__syncthreads_and(ok)) {
-        ok = false;
-        break;
+    while (issued < copied) {
+      const int s = issued % kWgStages;
+      if (fetch < last) {
+        // copied == issued + kWgStages - 1: the stage to refill was last read by tile issued - 1
+        if (issued >= 1)
+          ok = mbar_wait(&done[(issued - 1) % kWgStages], (uint32_t)(((issued - 1) / kWgStages) & 1), kWgWaitNs);
+        if (!ok) break;
+        stage_copy(fetch, copied % kWgStages);
+        fetch = next_live(fetch + 1);
+        ++copied;
       }
-      stage_copy(fetch, copied % kWgStages);
-      fetch = next_live(fetch + 1);
-      ++copied;
-    }
-    asm volatile("cp.async.commit_group;" ::: "memory");
-    asm volatile("cp.async.wait_group %0;" ::"n"(kWgStages - 1) : "memory");  // group `issued` landed
-    fence_proxy_async_smem();  // the copies are visible to the tensor cores
-    __syncthreads();
-    if (tid == 0) {
+      ok = mbar_wait(&full[s], (uint32_t)((issued / kWgStages) & 1), kWgWaitNs);
+      if (!ok) break;
       tc_fence_after();
       const uint32_t a0 = smem_u32(sm + s * kWgStage), b0 = a0 + kWgABytes;
       for (int j = 0; j < ntaps; ++j) {
@@ -156,26 +155,47 @@ __global__ void __launch_bounds__(kWgThreads, 1)
                       (issued > 0 || kk > 0) ? 1u : 0u);
       }
       tc_commit(&done[s]);
+      ++issued;
     }
-    ++issued;
+    // wait (bounded) for the last committed tile of each stage and for every copy armed
+    bool drained = true;
+    for (int k = issued - 1; k >= 0 && k >= issued - kWgStages; --k)
+      if (!mbar_wait(&done[k % kWgStages], (uint32_t)((k / kWgStages) & 1), kWgWaitNs)) drained = false;
+    for (int k = issued; k < copied; ++k)
+      if (!mbar_wait(&full[k % kWgStages], (uint32_t)((k / kWgStages) & 1), kWgWaitNs)) drained = false;
+    if (!ok || !drained) {
+      atomicOr(err, ERR_TIMEOUT);
+      issued = -1;
+    }
+    *s_issued = (uint32_t)issued;
   }
-  asm volatile("cp.async.wait_group 0;" ::: "memory");  // no copy in flight past this point
-  // wait for the last committed tile of each stage (bounded), then read the accumulators
-  bool drained = true;
-  for (int k = issued - 1; k >= 0 && k >= issued - kWgStages; --k)
-    if (!mbar_wait(&done[k % kWgStages], (uint32_t)((k / kWgStages) & 1), kWgWaitNs)) drained = false;
-  if (!ok || !drained) {
-    if (tid == 0) atomicOr(err, ERR_TIMEOUT);
-  } else if (issued > 0) {
+  __syncthreads();
+  const int issued = (int)*s_issued;
+  if (issued > 0) {
+    // every MMA has completed and no copy is in flight: the stage buffers are free.  Each
+    // warp turns its 32 x 32 blocks (thread = input channel) around in shared memory (rows
+    // padded to 33 floats) so that its atomic adds are 16-byte vectors along the output
+    // channels: a warp instruction covers 4 rows x 128 contiguous bytes.
     tc_fence_after();
+    float* st = reinterpret_cast<float*>(sm) + warp * 32 * 33;
     for (int j = 0; j < ntaps; ++j) {
-      float* dwt = dw + (int64_t)(t0 + j) * kPropC * kPropC + (int64_t)(warp * 32 + lane) * kPropC;
+      float* dwt = dw + (int64_t)(t0 + j) * kPropC * kPropC + (int64_t)(warp * 32) * kPropC;
       for (int c = 0; c < 128; c += 32) {
         uint32_t r[32];
         tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(j * 128 + c), r);
         tmem_wait_ld();
 #pragma unroll
-        for (int q = 0; q < 32; ++q) atomicAdd(dwt + c + q, __uint_as_float(r[q]));
+        for (int q = 0; q < 32; ++q) st[lane * 33 + q] = __uint_as_float(r[q]);
+        __syncwarp();
+        const int c4 = 4 * (lane & 7);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int i = (lane >> 3) + 4 * k;
+          const float* row = st + i * 33 + c4;
+          atomicAdd(reinterpret_cast<float4*>(dwt + (int64_t)i * kPropC + c + c4),
+                    make_float4(row[0], row[1], row[2], row[3]));
+        }
+        __syncwarp();
       }
     }
   }
@@ -200,12 +220,16 @@ cudaError_t prop_conv_wgrad_tc(const __nv_bfloat16* in, const __nv_bfloat16* g, 
   if (e != cudaSuccess) return e;
   const int64_t total = (int64_t)n * ((rows - 6) / kWgTile);
   if (total <= 0) return cudaSuccess;
+  CUtensorMap tin, tg;
+  e = prop_tensor_map_rows(&tin, in, (int64_t)n * rows, 8, (uint32_t)kWgABox, false);
+  if (e == cudaSuccess) e = prop_tensor_map_rows(&tg, g, (int64_t)n * rows, 8, (uint32_t)kWgTile, false);
+  if (e != cudaSuccess) return e;
   const int groups = (kPropTaps + kWgTapsPerCta - 1) / kWgTapsPerCta;
   // about one CTA per SM: runs of tiles per tap group
   const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>(total, (num_sms + groups - 1) / groups));
   const int32_t per = (int32_t)((total + ctas - 1) / ctas);
   dim3 grid((unsigned)((total + per - 1) / per), (unsigned)groups);
-  k_conv_wgrad_tc<<<grid, kWgThreads, kWgSmem, s>>>(in, g, lens, dw, n, rows, per, err);
+  k_conv_wgrad_tc<<<grid, kWgThreads, kWgSmem, s>>>(tin, tg, lens, dw, n, rows, per, err);
   return cudaGetLastError();
 }
 
