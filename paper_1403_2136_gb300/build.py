@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmaxss.so")
-SOURCES = ["api.cu", "pack.cu", "scan.cu", "nw.cu", "probe.cu", "nw_noalloc.cu", "prop.cu", "prop_api.cu", "rescore.cu", "score_tc.cu", "sam.cu", "conv_tc.cu", "wgrad_tc.cu"]
+SOURCES = ["api.cu", "pack.cu", "scan.cu", "nw.cu", "probe.cu", "nw_noalloc.cu", "prop.cu", "prop_api.cu", "rescore.cu", "score_tc.cu", "sam.cu", "conv_tc.cu", "wgrad_tc.cu", "embed_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr"]

@@ -7,9 +7,8 @@
 // accumulation FP32.
 //
 // Kernels here (the 128 -> 128 conv itself, forward and backward-data, runs on the
-// fifth-generation tensor cores in conv_tc.cu, its weight gradient in wgrad_tc.cu, the read x
-// fragment score GEMM with its fused top K in score_tc.cu):
-//   k_embed_l1      first layer (4 -> 128) as a gather-sum of per-base weight rows
+// fifth-generation tensor cores in conv_tc.cu, its weight gradient in wgrad_tc.cu, the first
+// layer in embed_tc.cu, the read x fragment score GEMM with its fused top K in score_tc.cu):
 //   k_pool_norm     max (first argmax kept) or mean over positions, L2 norm
 //   k_pool_norm_bwd gradient of the norm routed to the argmax positions (max) or spread
 //                   over the positions with weight 1 / length (mean)
@@ -28,54 +27,6 @@
 #include "tc.cuh"
 
 namespace mss {
-
-// ------------------------------------------------------------------------------------------
-// layer 1: out[n][p][co] = relu(b[co] + sum_t w1[t][x[p+t-3]][co]) for p < len, else 0
-// thread = (position, group of 8 channels); a CTA covers 64 positions of one sequence, 16 at a
-// time; the per-channel sums run in the same order as the definition (bias, then taps 0 .. 6)
-constexpr int kL1Pos = 64;
-__global__ void __launch_bounds__(256) k_embed_l1(const uint8_t* __restrict__ codes, const int32_t* __restrict__ lens,
-                                                  int32_t ld_codes, const float* __restrict__ w1,
-                                                  const float* __restrict__ b1, __nv_bfloat16* __restrict__ out,
-                                                  int32_t rows) {
-  const int n = blockIdx.y;
-  const int g = threadIdx.x & 15;
-  const int len = lens[n];
-  const int p_end = min(rows - 6, (int)(blockIdx.x + 1) * kL1Pos);
-  const uint8_t* cn = codes + (int64_t)n * ld_codes;
-  for (int p = blockIdx.x * kL1Pos + (threadIdx.x >> 4); p < p_end; p += 16) {
-    float v[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) v[j] = 0.f;
-    if (p < len) {
-      const float4 bA = *reinterpret_cast<const float4*>(b1 + 8 * g);
-      const float4 bB = *reinterpret_cast<const float4*>(b1 + 8 * g + 4);
-      v[0] = bA.x, v[1] = bA.y, v[2] = bA.z, v[3] = bA.w, v[4] = bB.x, v[5] = bB.y, v[6] = bB.z, v[7] = bB.w;
-#pragma unroll
-      for (int t = 0; t < kPropTaps; ++t) {
-        const int q = p + t - 3;
-        if (q >= 0 && q < len) {
-          const uint32_t c = cn[q];
-          if (c < 4) {
-            const float4* wr = reinterpret_cast<const float4*>(w1 + (t * 4 + c) * kPropC + 8 * g);
-            const float4 wA = wr[0], wB = wr[1];
-            v[0] += wA.x, v[1] += wA.y, v[2] += wA.z, v[3] += wA.w;
-            v[4] += wB.x, v[5] += wB.y, v[6] += wB.z, v[7] += wB.w;
-          }
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < 8; ++j) v[j] = fmaxf(v[j], 0.f);
-    }
-    uint32_t w[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-      w[j] = *reinterpret_cast<uint32_t*>(&h);
-    }
-    *reinterpret_cast<uint4*>(out + ((int64_t)n * rows + p + 3) * kPropC + 8 * g) = make_uint4(w[0], w[1], w[2], w[3]);
-  }
-}
 
 // zero the three halo rows on each side of every sequence of up to four activation buffers
 // (the layers write every other row)
@@ -469,13 +420,6 @@ __global__ void k_topk(const float* __restrict__ scores, int64_t NF, int32_t K, 
 
 // ------------------------------------------------------------------------------------------
 // host launchers
-cudaError_t prop_embed_l1(const uint8_t* codes, const int32_t* lens, int32_t ld, int32_t n, const float* w1,
-                          const float* b1, __nv_bfloat16* out, int32_t rows, cudaStream_t s) {
-  dim3 grid((unsigned)((rows - 6 + kL1Pos - 1) / kL1Pos), (unsigned)n);
-  k_embed_l1<<<grid, 256, 0, s>>>(codes, lens, ld, w1, b1, out, rows);
-  return cudaGetLastError();
-}
-
 cudaError_t prop_zero_halo(__nv_bfloat16* b0, __nv_bfloat16* b1, __nv_bfloat16* b2, __nv_bfloat16* b3, int32_t n,
                            int32_t rows, cudaStream_t s) {
   const int64_t work = (int64_t)n * 96;

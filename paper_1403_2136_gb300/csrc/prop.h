@@ -31,8 +31,9 @@ inline int32_t prop_rows(int32_t maxlen) { return ((maxlen + 127) / 128) * 128 +
 // zero the 3 halo rows on each side of every sequence of up to four activation buffers (null = skip)
 cudaError_t prop_zero_halo(__nv_bfloat16* b0, __nv_bfloat16* b1, __nv_bfloat16* b2, __nv_bfloat16* b3, int32_t n,
                            int32_t rows, cudaStream_t s);
+// first layer on the tensor cores (embed_tc.cu); err: device error word (bounded waits)
 cudaError_t prop_embed_l1(const uint8_t* codes, const int32_t* lens, int32_t ld, int32_t n, const float* w1,
-                          const float* b1, __nv_bfloat16* out, int32_t rows, cudaStream_t s);
+                          const float* b1, __nv_bfloat16* out, int32_t rows, int32_t* err, cudaStream_t s);
 // 128 -> 128 conv on the tensor cores (conv_tc.cu).  wcanon: the layer's weights w[t][in][out]
 // rearranged by prop_canon_weights (prop_canon_weight_bytes() bytes).  mode 0: out =
 // relu(conv + bias) for p < len; mode 1 (backward data, flipped weights): out = conv where

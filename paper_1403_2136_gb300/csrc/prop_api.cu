@@ -113,7 +113,9 @@ mss_status forward(mss_prop* p, const uint8_t* codes, const int32_t* lens, int32
                      a.act[3].as<__nv_bfloat16>(), n, rows, s),
       "activation halo");
   const float* w = p->w32.as<float>();
-  PCK(prop_embed_l1(codes, lens, ld, n, w, w + prop_off_b1(), a.act[0].as<__nv_bfloat16>(), rows, s), "layer 1");
+  PCK(prop_embed_l1(codes, lens, ld, n, w, w + prop_off_b1(), a.act[0].as<__nv_bfloat16>(), rows,
+                    p->err.as<int32_t>(), s),
+      "layer 1");
   for (int l = 2; l <= 4; ++l)
     PCK(prop_conv_tc(a.act[l - 2].as<__nv_bfloat16>(), p->wct[l - 2].p, w + prop_off_b(l), nullptr, lens,
                      a.act[l - 1].as<__nv_bfloat16>(), n, rows, 0, p->err.as<int32_t>(), s),
