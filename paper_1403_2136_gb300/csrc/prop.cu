@@ -7,12 +7,11 @@
 // accumulation FP32.
 //
 // Kernels here (the 128 -> 128 conv itself, forward and backward-data, runs on the
-// fifth-generation tensor cores in conv_tc.cu, its weight gradient in wgrad_tc.cu, the first
-// layer in embed_tc.cu, the read x fragment score GEMM with its fused top K in score_tc.cu):
+// fifth-generation tensor cores in conv_tc.cu, the weight and bias gradients of all layers in
+// wgrad_tc.cu, the first layer in embed_tc.cu, the read x fragment score GEMM with its fused top K in score_tc.cu):
 //   k_pool_norm     max (first argmax kept) or mean over positions, L2 norm
 //   k_pool_norm_bwd gradient of the norm routed to the argmax positions (max) or spread
 //                   over the positions with weight 1 / length (mean)
-//   k_l1_wgrad      first-layer weight/bias gradients; k_bias_grad: bias gradients
 //   k_ce_loss       softmax cross-entropy of read-vs-candidate logits and its gradients
 //   k_adamw         AdamW on FP32 master weights, refreshing the BF16 copies
 //   k_scores        read x fragment scores (max over the read's two strands)
@@ -45,48 +44,6 @@ __global__ void k_zero_halo(__nv_bfloat16* b0, __nv_bfloat16* b1, __nv_bfloat16*
 }
 
 // ------------------------------------------------------------------------------------------
-// bias gradient: db[co] += sum_{n, p < len} g[n][p + 3][co]
-__global__ void k_bias_grad(const __nv_bfloat16* __restrict__ g, const int32_t* __restrict__ lens, float* db,
-                            int32_t rows) {
-  const int n = blockIdx.y, co = threadIdx.x & 127, half = threadIdx.x >> 7;
-  const int len = lens[n];
-  float s = 0.f;
-  for (int p = blockIdx.x * 2 + half; p < len; p += gridDim.x * 2)
-    s += __bfloat162float(g[((int64_t)n * rows + p + 3) * kPropC + co]);
-  atomicAdd(db + co, s);
-}
-
-// first layer gradients: dw1[t][c][co] += g[p][co] for x[p + t - 3] == c; db1[co] += g[p][co]
-__global__ void k_l1_wgrad(const uint8_t* __restrict__ codes, const int32_t* __restrict__ lens, int32_t ld_codes,
-                           const __nv_bfloat16* __restrict__ g, float* dw1, float* db1, int32_t rows) {
-  __shared__ float s_w[kPropTaps * 4][kPropC];
-  __shared__ float s_b[kPropC];
-  const int n = blockIdx.y, co = threadIdx.x;
-  for (int e = threadIdx.x; e < kPropTaps * 4 * kPropC; e += blockDim.x) (&s_w[0][0])[e] = 0.f;
-  if (co < kPropC) s_b[co] = 0.f;
-  __syncthreads();
-  const int len = lens[n];
-  for (int p = blockIdx.x; p < len; p += gridDim.x) {
-    const float gv = __bfloat162float(g[((int64_t)n * rows + p + 3) * kPropC + co]);
-    if (gv == 0.f) continue;
-    s_b[co] += gv;
-#pragma unroll
-    for (int t = 0; t < kPropTaps; ++t) {
-      const int q = p + t - 3;
-      if (q >= 0 && q < len) {
-        const uint32_t c = codes[(int64_t)n * ld_codes + q];
-        if (c < 4) s_w[t * 4 + c][co] += gv;
-      }
-    }
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < kPropTaps * 4 * kPropC; e += blockDim.x) {
-    const float v = (&s_w[0][0])[e];
-    if (v != 0.f) atomicAdd(dw1 + e, v);
-  }
-  if (s_b[co] != 0.f) atomicAdd(db1 + co, s_b[co]);
-}
-
 // ------------------------------------------------------------------------------------------
 // pool over the positions p < len of each channel, then the L2 norm.  CTA = one sequence,
 // 256 threads = 16 position lanes x 16 groups of 8 channels.  Max: the lanes' maxima merge
@@ -428,20 +385,6 @@ cudaError_t prop_zero_halo(__nv_bfloat16* b0, __nv_bfloat16* b1, __nv_bfloat16* 
   return cudaGetLastError();
 }
 
-
-cudaError_t prop_bias_grad(const __nv_bfloat16* g, const int32_t* lens, float* db, int32_t n, int32_t rows,
-                           cudaStream_t s) {
-  dim3 grid(16, (unsigned)n);
-  k_bias_grad<<<grid, 256, 0, s>>>(g, lens, db, rows);
-  return cudaGetLastError();
-}
-
-cudaError_t prop_l1_wgrad(const uint8_t* codes, const int32_t* lens, int32_t ld, const __nv_bfloat16* g, float* dw1,
-                          float* db1, int32_t n, int32_t rows, cudaStream_t s) {
-  dim3 grid(2, (unsigned)n);
-  k_l1_wgrad<<<grid, kPropC, 0, s>>>(codes, lens, ld, g, dw1, db1, rows);
-  return cudaGetLastError();
-}
 
 cudaError_t prop_pool_norm(const __nv_bfloat16* act, const int32_t* lens, int32_t n, int32_t rows, float* emb,
                            float* norms, int32_t* argmax, int32_t mean, cudaStream_t s) {

@@ -44,14 +44,14 @@ cudaError_t prop_conv_tc(const __nv_bfloat16* in, const void* wcanon, const floa
                          const int32_t* lens, __nv_bfloat16* out, int32_t n, int32_t rows, int mode, int32_t* err,
                          cudaStream_t s);
 // Weight gradient of a 128 -> 128 layer, dw[t][ci][co] += sum over sequences and positions p
-// of in[p + t - 3][ci] * g[p][co], on the fifth-generation tensor cores (wgrad_tc.cu); err:
-// device error word (a bounded wait that gives up sets ERR_TIMEOUT).
+// of in[p + t - 3][ci] * g[p][co], and (db not null) its bias gradient db[co] += sum of
+// g[p][co], on the fifth-generation tensor cores (wgrad_tc.cu); err: device error word (a
+// bounded wait that gives up sets ERR_TIMEOUT).
 cudaError_t prop_conv_wgrad_tc(const __nv_bfloat16* in, const __nv_bfloat16* g, const int32_t* lens, float* dw,
-                               int32_t n, int32_t rows, int32_t* err, cudaStream_t s);
-cudaError_t prop_bias_grad(const __nv_bfloat16* g, const int32_t* lens, float* db, int32_t n, int32_t rows,
-                           cudaStream_t s);
+                               float* db, int32_t n, int32_t rows, int32_t* err, cudaStream_t s);
+// first-layer weight and bias gradients on the tensor cores (wgrad_tc.cu); err: device error word
 cudaError_t prop_l1_wgrad(const uint8_t* codes, const int32_t* lens, int32_t ld, const __nv_bfloat16* g, float* dw1,
-                          float* db1, int32_t n, int32_t rows, cudaStream_t s);
+                          float* db1, int32_t n, int32_t rows, int32_t* err, cudaStream_t s);
 cudaError_t prop_pool_norm(const __nv_bfloat16* act, const int32_t* lens, int32_t n, int32_t rows, float* emb,
                            float* norms, int32_t* argmax, int32_t mean, cudaStream_t s);
 cudaError_t prop_pool_norm_bwd(const float* emb, const float* demb, const float* norms, const int32_t* argmax,

@@ -145,17 +145,16 @@ mss_status backward(mss_prop* p, const uint8_t* codes, const int32_t* lens, int3
   p->launches += 1;
   for (int l = 4; l >= 2; --l) {
     // gcur = gradient of layer l's pre-activation; input activation of layer l is act[l - 2]
-    PCK(prop_conv_wgrad_tc(a.act[l - 2].as<__nv_bfloat16>(), gcur, lens, gw + prop_off_w(l), n, rows,
-                           p->err.as<int32_t>(), s),
-        "wgrad");
-    PCK(prop_bias_grad(gcur, lens, gw + prop_off_b(l), n, rows, s), "bias grad");
+    PCK(prop_conv_wgrad_tc(a.act[l - 2].as<__nv_bfloat16>(), gcur, lens, gw + prop_off_w(l), gw + prop_off_b(l), n,
+                           rows, p->err.as<int32_t>(), s),
+        "weight and bias gradients");
     PCK(prop_conv_tc(gcur, p->wfct[l - 2].p, nullptr, a.act[l - 2].as<__nv_bfloat16>(), lens, gnext, n, rows, 1,
                      p->err.as<int32_t>(), s),
         "conv backward");
     std::swap(gcur, gnext);
-    p->launches += 3;
+    p->launches += 2;
   }
-  PCK(prop_l1_wgrad(codes, lens, ld, gcur, gw, gw + prop_off_b1(), n, rows, s), "layer 1 grad");
+  PCK(prop_l1_wgrad(codes, lens, ld, gcur, gw, gw + prop_off_b1(), n, rows, p->err.as<int32_t>(), s), "layer 1 grad");
   p->launches += 1;
   return MSS_OK;
 }

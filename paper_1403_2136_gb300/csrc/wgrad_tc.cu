@@ -15,9 +15,12 @@
 // row) sits at channel-group * stride + row * 16, rows are 16 bytes apart throughout, and a
 // tap's shift is a start-address offset of 16 bytes per row.  The same thread issues, per
 // tap, eight tcgen05.mma (K = 16 positions each) and commits them on the stage's mbarrier,
-// which the next copy into that stage waits for.  At the end the four warps read their 32
-// accumulator lanes (input channels) back and add them to dw with 16-byte FP32 atomics along
-// the output channels.  Every wait is bounded.
+// which the next copy into that stage waits for.  The CTAs of the three-tap group also
+// accumulate the bias gradient db[co] = sum over positions of g[p][co] in their free fourth
+// accumulator, as one more MMA per K-step with an operand of ones (every row of that
+// accumulator is the column sum).  At the end the four warps read their 32 accumulator lanes
+// (input channels) back and add them to dw with 16-byte FP32 atomics along the output
+// channels.  Every wait is bounded.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -44,7 +47,9 @@ constexpr uint32_t kWgBBytes = 16 * kWgBStride;           // 32,768
 constexpr uint32_t kWgStage = kWgABytes + kWgBBytes;
 constexpr uint32_t kWgTx = 16 * (kWgABox + kWgTile) * 16; // bytes landing per tile
 constexpr int kWgStages = 3;                              // copies two tiles ahead
-constexpr uint32_t kWgSmem = kWgStages * kWgStage + 64;   // stages, mbarriers, TMEM slot
+constexpr uint32_t kWgOnes = kWgStages * kWgStage;         // 4 KB of BF16 ones (bias operand)
+constexpr uint32_t kWgOnesBytes = 4096;
+constexpr uint32_t kWgSmem = kWgOnes + kWgOnesBytes + 64;  // stages, ones, mbarriers, TMEM slot
 constexpr uint64_t kWgWaitNs = 2000000000ull;
 static_assert(kWgAStride % 128 == 0 && kWgBStride % 128 == 0 && kWgStage % 128 == 0, "TMA destinations");
 // MN-major operands without swizzling: core matrices of 8 rows (K) x 16 bytes (8 MN
@@ -68,10 +73,11 @@ __device__ __forceinline__ void tma_tile_2d(uint32_t dst, const CUtensorMap* map
 
 __global__ void __launch_bounds__(kWgThreads, 1)
     k_conv_wgrad_tc(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tg,
-                    const int32_t* __restrict__ lens, float* __restrict__ dw, int32_t n_seq, int32_t rows,
+                    const int32_t* __restrict__ lens, float* __restrict__ dw, float* __restrict__ db,
+                    int32_t n_seq, int32_t rows,
                     int32_t tiles_per_cta, int32_t* err) {
   extern __shared__ __align__(1024) uint8_t sm[];
-  uint64_t* full = reinterpret_cast<uint64_t*>(sm + kWgStages * kWgStage);       // [kWgStages]
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + kWgOnes + kWgOnesBytes);      // [kWgStages]
   uint64_t* done = full + kWgStages;                                              // [kWgStages]
   uint32_t* s_tmem = reinterpret_cast<uint32_t*>(done + kWgStages);
   uint32_t* s_issued = s_tmem + 1;
@@ -82,6 +88,11 @@ __global__ void __launch_bounds__(kWgThreads, 1)
   const int64_t total = (int64_t)n_seq * tiles_per_seq;
   const int64_t first = (int64_t)blockIdx.x * tiles_per_cta;
   const int64_t last = min(total, first + tiles_per_cta);
+  // the three-tap group's free accumulator (columns 384 ..) takes the bias gradient
+  const bool with_bias = db != nullptr && ntaps < kWgTapsPerCta;
+  for (int e = tid; e < (int)(kWgOnesBytes / 4); e += kWgThreads)
+    reinterpret_cast<uint32_t*>(sm + kWgOnes)[e] = 0x3F803F80u;  // BF16 1.0, 1.0
+  fence_proxy_async_smem();
 
   if (tid == 0) {
     for (int k = 0; k < kWgStages; ++k) {
@@ -154,6 +165,16 @@ __global__ void __launch_bounds__(kWgThreads, 1)
                       smem_desc(b0 + (uint32_t)(16 * kk) * 16, kWgCoreK, kWgBStride), kWgIdesc,
                       (issued > 0 || kk > 0) ? 1u : 0u);
       }
+      if (with_bias) {
+        // ones [K = 16 positions][M = 128]: any layout of the 4 KB of ones; leading offset
+        // 128 B, stride offset 256 B keep the 2 x 16 core matrices inside it
+        const uint64_t ones = smem_desc(smem_u32(sm + kWgOnes), kWgCoreK, 256);
+#pragma unroll
+        for (int kk = 0; kk < kWgTile / 16; ++kk)
+          tc_mma_bf16(tmem + (uint32_t)(kWgTapsPerCta - 1) * 128, ones,
+                      smem_desc(b0 + (uint32_t)(16 * kk) * 16, kWgCoreK, kWgBStride), kWgIdesc,
+                      (issued > 0 || kk > 0) ? 1u : 0u);
+      }
       tc_commit(&done[s]);
       ++issued;
     }
@@ -199,15 +220,194 @@ __global__ void __launch_bounds__(kWgThreads, 1)
       }
     }
   }
+  if (issued > 0 && with_bias && warp == 0) {  // row 0 of the ones accumulator: lane 0 of warp 0
+    for (int c = 0; c < 128; c += 32) {
+      uint32_t r[32];
+      tmem_ld32(tmem + (uint32_t)(kWgTapsPerCta - 1) * 128 + (uint32_t)c, r);
+      tmem_wait_ld();
+      if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < 32; ++q) atomicAdd(db + c + q, __uint_as_float(r[q]));
+    }
+  }
   tc_fence_before();
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, 512);
 }
 
+// First-layer gradients on the tensor cores: dw1[4t + b][co] += sum over positions p of
+// [x[p + t - 3] = b] * g[p][co] and db1[co] += sum of g[p][co], as the GEMM
+// D[f][co] = sum_p F[p][f] g[p][co] with the one-hot features F (f = 4t + b < 28, f = 28 all
+// ones, the rest zero) as an MN-major A operand built from the codes (M = 128, rows 29.. zero)
+// and the gradient tiles as B, staged by TMA exactly as for the other layers.  Warps 1-3 build
+// A; thread 0 stages B and issues the 8 MMAs per tile into one 128-column accumulator.
+constexpr int kL1gStages = 3;
+constexpr uint32_t kL1gSmem = kL1gStages * kWgStage + 128;
+
+__global__ void __launch_bounds__(kWgThreads, 1)
+    k_l1_wgrad_tc(const __grid_constant__ CUtensorMap tg, const uint8_t* __restrict__ codes, int32_t ld,
+                  const int32_t* __restrict__ lens, float* __restrict__ dw1, float* __restrict__ db1, int32_t n_seq,
+                  int32_t rows, int32_t tiles_per_cta, int32_t* err) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + kL1gStages * kWgStage);  // [3] B landed
+  uint64_t* built = full + kL1gStages;                                       // [3] A built (3 warps)
+  uint64_t* done = built + kL1gStages;                                       // [3] MMAs completed
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(done + kL1gStages);
+  uint32_t* s_issued = s_tmem + 1;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tiles_per_seq = (rows - 6) / kWgTile;
+  const int64_t total = (int64_t)n_seq * tiles_per_seq;
+  const int64_t first = (int64_t)blockIdx.x * tiles_per_cta;
+  const int64_t last = min(total, first + tiles_per_cta);
+  if (tid == 0) {
+    for (int k = 0; k < kL1gStages; ++k) {
+      mbar_init(&full[k], 1);
+      mbar_init(&built[k], 3);
+      mbar_init(&done[k], 1);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    tmem_alloc(s_tmem, 128);
+    tmem_relinquish();
+  }
+  // the feature rows 32 .. 127 of every stage's A stay zero
+  for (int e = tid; e < kL1gStages * 12 * (int)kWgAStride / 16; e += kWgThreads) {
+    const int st = e / (12 * (int)kWgAStride / 16), rem = e - st * (12 * (int)kWgAStride / 16);
+    *reinterpret_cast<uint4*>(sm + st * kWgStage + 4 * kWgAStride + rem * 16) = make_uint4(0, 0, 0, 0);
+  }
+  fence_proxy_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *s_tmem;
+  auto next_live = [&](int64_t tile) {
+    while (tile < last) {
+      const int n = (int)(tile / tiles_per_seq);
+      if ((int)(tile - (int64_t)n * tiles_per_seq) * kWgTile < lens[n]) break;
+      ++tile;
+    }
+    return tile;
+  };
+
+  if (tid == 0) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tg)) : "memory");
+    bool ok = true;
+    int issued = 0, copied = 0;
+    int64_t fetch = next_live(first);
+    auto stage_copy = [&](int64_t tile, int s) {
+      const int n = (int)(tile / tiles_per_seq);
+      const int p0 = (int)(tile - (int64_t)n * tiles_per_seq) * kWgTile;
+      const uint32_t sB = smem_u32(sm + s * kWgStage) + kWgABytes;
+      mbar_arrive_expect_tx(&full[s], 16 * kWgTile * 16);
+      for (int c = 0; c < 16; ++c) tma_tile_2d(sB + c * kWgBStride, &tg, 8 * c, n * rows + p0 + 3, &full[s]);
+    };
+    for (int k = 0; k < kL1gStages - 1 && fetch < last; ++k) {
+      stage_copy(fetch, k);
+      fetch = next_live(fetch + 1);
+      ++copied;
+    }
+    while (issued < copied) {
+      const int s = issued % kL1gStages;
+      if (fetch < last) {
+        if (issued >= 1)
+          ok = mbar_wait(&done[(issued - 1) % kL1gStages], (uint32_t)(((issued - 1) / kL1gStages) & 1), kWgWaitNs);
+        if (!ok) break;
+        stage_copy(fetch, copied % kL1gStages);
+        fetch = next_live(fetch + 1);
+        ++copied;
+      }
+      const uint32_t par = (uint32_t)((issued / kL1gStages) & 1);
+      ok = mbar_wait(&full[s], par, kWgWaitNs) && mbar_wait(&built[s], par, kWgWaitNs);
+      if (!ok) break;
+      tc_fence_after();
+      const uint32_t a0 = smem_u32(sm + s * kWgStage), b0 = a0 + kWgABytes;
+#pragma unroll
+      for (int kk = 0; kk < kWgTile / 16; ++kk)
+        tc_mma_bf16(tmem, smem_desc(a0 + (uint32_t)(16 * kk) * 16, kWgCoreK, kWgAStride),
+                    smem_desc(b0 + (uint32_t)(16 * kk) * 16, kWgCoreK, kWgBStride), kWgIdesc,
+                    (issued > 0 || kk > 0) ? 1u : 0u);
+      tc_commit(&done[s]);
+      ++issued;
+    }
+    bool drained = true;
+    for (int k = issued - 1; k >= 0 && k >= issued - kL1gStages; --k)
+      if (!mbar_wait(&done[k % kL1gStages], (uint32_t)((k / kL1gStages) & 1), kWgWaitNs)) drained = false;
+    for (int k = issued; k < copied; ++k)
+      if (!mbar_wait(&full[k % kL1gStages], (uint32_t)((k / kL1gStages) & 1), kWgWaitNs)) drained = false;
+    if (!ok || !drained) {
+      atomicOr(err, ERR_TIMEOUT);
+      issued = -1;
+    }
+    *s_issued = (uint32_t)issued;
+  } else if (warp >= 1) {
+    // A builders: live tile k in stage k mod 3; chunk (row r = position p0 + r, feature group
+    // c < 4) holds features 8c .. 8c + 7 (taps 2c and 2c + 1; group 3: tap 6 and the ones)
+    bool ok = true;
+    int k = 0;
+    for (int64_t tile = next_live(first); tile < last; tile = next_live(tile + 1), ++k) {
+      const int s = k % kL1gStages;
+      if (k >= kL1gStages && ok)
+        ok = __all_sync(0xffffffffu,
+                        mbar_wait(&done[s], (uint32_t)(((k - kL1gStages) / kL1gStages) & 1), kWgWaitNs));
+      if (ok) {
+        const int n = (int)(tile / tiles_per_seq);
+        const int p0 = (int)(tile - (int64_t)n * tiles_per_seq) * kWgTile;
+        const int len = lens[n];
+        const uint8_t* cn = codes + (int64_t)n * ld;
+        uint8_t* a = sm + s * kWgStage;
+        for (int e = tid - 32; e < kWgTile * 4; e += kWgThreads - 32) {
+          const int r = e >> 2, c = e & 3;
+          uint32_t w[4];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int t = 2 * c + h, q = p0 + r + t - 3;
+            uint32_t cd = (t < kPropTaps && q >= 0 && q < len) ? (uint32_t)cn[q] : 4u;
+            w[2 * h] = (cd == 0u ? 0x3F80u : 0u) | (cd == 1u ? 0x3F800000u : 0u);
+            w[2 * h + 1] = (cd == 2u ? 0x3F80u : 0u) | (cd == 3u ? 0x3F800000u : 0u);
+          }
+          if (c == 3) w[2] = 0x3F80u, w[3] = 0u;  // feature 28: ones; 29-31: zero
+          *reinterpret_cast<uint4*>(a + c * kWgAStride + r * 16) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+        fence_proxy_async_smem();
+      } else if (lane == 0) {
+        atomicOr(err, ERR_TIMEOUT);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&built[s]);
+    }
+  }
+  __syncthreads();
+  const int issued = (int)*s_issued;
+  if (issued > 0) {
+    // rows 0..28 of the accumulator (warp 0's lanes) through shared memory, then coalesced
+    // atomic adds along the output channels
+    tc_fence_after();
+    float* st = reinterpret_cast<float*>(sm);  // [29][129]
+    if (warp == 0)
+      for (int c = 0; c < 128; c += 32) {
+        uint32_t r[32];
+        tmem_ld32(tmem + (uint32_t)c, r);
+        tmem_wait_ld();
+        if (lane < 29)
+#pragma unroll
+          for (int q = 0; q < 32; ++q) st[lane * 129 + c + q] = __uint_as_float(r[q]);
+      }
+    __syncthreads();
+    for (int f = 0; f < 29; ++f) {
+      const float v = st[f * 129 + tid];
+      if (v != 0.f) atomicAdd(f < 28 ? dw1 + f * kPropC + tid : db1 + tid, v);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, 128);
+}
+
 }  // namespace
 
 cudaError_t prop_conv_wgrad_tc(const __nv_bfloat16* in, const __nv_bfloat16* g, const int32_t* lens, float* dw,
-                               int32_t n, int32_t rows, int32_t* err, cudaStream_t s) {
+                               float* db, int32_t n, int32_t rows, int32_t* err, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k_conv_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgSmem);
@@ -229,7 +429,35 @@ cudaError_t prop_conv_wgrad_tc(const __nv_bfloat16* in, const __nv_bfloat16* g, 
   const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>(total, (num_sms + groups - 1) / groups));
   const int32_t per = (int32_t)((total + ctas - 1) / ctas);
   dim3 grid((unsigned)((total + per - 1) / per), (unsigned)groups);
-  k_conv_wgrad_tc<<<grid, kWgThreads, kWgSmem, s>>>(tin, tg, lens, dw, n, rows, per, err);
+  k_conv_wgrad_tc<<<grid, kWgThreads, kWgSmem, s>>>(tin, tg, lens, dw, db, n, rows, per, err);
+  return cudaGetLastError();
+}
+
+}  // namespace mss
+
+namespace mss {
+
+cudaError_t prop_l1_wgrad(const uint8_t* codes, const int32_t* lens, int32_t ld, const __nv_bfloat16* g, float* dw1,
+                          float* db1, int32_t n, int32_t rows, int32_t* err, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_l1_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kL1gSmem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  int dev = 0, num_sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const int64_t total = (int64_t)n * ((rows - 6) / kWgTile);
+  if (total <= 0) return cudaSuccess;
+  CUtensorMap tg;
+  e = prop_tensor_map_rows(&tg, g, (int64_t)n * rows, 8, (uint32_t)kWgTile, false);
+  if (e != cudaSuccess) return e;
+  const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>(total, num_sms));
+  const int32_t per = (int32_t)((total + ctas - 1) / ctas);
+  k_l1_wgrad_tc<<<(unsigned)((total + per - 1) / per), kWgThreads, kL1gSmem, s>>>(tg, codes, ld, lens, dw1, db1, n, rows,
+                                                                                 per, err);
   return cudaGetLastError();
 }
 
