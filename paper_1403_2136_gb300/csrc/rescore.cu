@@ -8,10 +8,11 @@
 // neighbour rule of the context the second is the best candidate not adjacent to the best.
 //
 // k_rescore_scan: one CTA per read; the read's two strands sit in a shared-memory profile;
-// each pass covers 2048 diagonals of one candidate (256 threads x 4 packed lane pairs (d,
-// d + 4) per strand), with the genome window expanded into PRMT selector words laid out
-// [position mod 8][position div 8] and the recurrence in packed 16-bit lanes (f16 FMA-relu
-// when exact, else int16 DPX add-max), as in the exhaustive scan.
+// each pass covers 2048 diagonals of two candidates at once (each half of the CTA: 128
+// threads x 8 packed lane pairs (d, d + 8) per strand), with each half's genome window
+// expanded into PRMT selector words laid out [position mod 16][position div 16] (four
+// positions' codes per multiply, as in the exhaustive scan) and the recurrence in packed
+// 16-bit lanes (f16 FMA-relu when exact, else int16 DPX add-max), as in the exhaustive scan.
 // k_rescore_pick: one warp per read; top-2 over the candidate maxima, then a plain int32
 // rescan of the best fragment for its best diagonal and strand.
 #include <algorithm>
@@ -25,10 +26,16 @@ namespace mss {
 
 namespace {
 
+template <bool B>
+struct BoolTagRs {
+  static constexpr bool value = B;
+};
+
 constexpr int kRsThreads = 256;
-constexpr int kRsD = 4;                         // lane pairs per thread and strand
+constexpr int kRsHalf = kRsThreads / 2;         // threads per candidate
+constexpr int kRsD = 8;                         // lane pairs per thread and strand
 constexpr int kRsSpan = 2 * kRsD;               // diagonals per thread
-constexpr int kRsTile = kRsThreads * kRsSpan;   // diagonals per pass
+constexpr int kRsTile = kRsHalf * kRsSpan;      // diagonals per pass and candidate (2048)
 
 struct RsArgs {
   const uint32_t* g2;
@@ -54,13 +61,14 @@ __host__ __device__ inline size_t rs_prof_bytes(int32_t max_len) {
 }
 inline int rs_cols(int32_t max_len) { return (kRsTile + rs_mpad(max_len) + 2 * kRsD + kRsSpan - 1) / kRsSpan; }
 inline size_t rs_smem(int32_t max_len) {
-  return rs_prof_bytes(max_len) + (size_t)kRsSpan * rs_cols(max_len) * 4 + 16;
+  return rs_prof_bytes(max_len) + 2 * (size_t)kRsSpan * rs_cols(max_len) * 4 + 16;
 }
 
 template <bool F16>
-__global__ void __launch_bounds__(kRsThreads, 4) k_rescore_scan(RsArgs a) {
+__global__ void __launch_bounds__(kRsThreads, 3) k_rescore_scan(RsArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int tid = threadIdx.x, lane = tid & 31;
+  const int half = tid >> 7, ltid = tid & (kRsHalf - 1);
   const int i = blockIdx.x;
   const int ridx = a.idx ? a.idx[i] : i;
   const int64_t off = a.offsets[ridx];
@@ -69,9 +77,9 @@ __global__ void __launch_bounds__(kRsThreads, 4) k_rescore_scan(RsArgs a) {
   if (l > a.max_len && tid == 0) atomicOr(a.err, ERR_BAD_LEN);
   const int mpad = max(kRsD, (m + kRsD - 1) / kRsD * kRsD);
   const int W = a.W;
-  uint32_t* prof = reinterpret_cast<uint32_t*>(smem);                       // [mpad + 1][2]
-  uint32_t* sel = reinterpret_cast<uint32_t*>(smem + rs_prof_bytes(a.max_len));  // [kRsSpan][W]
-  int32_t* s_best = reinterpret_cast<int32_t*>(sel + kRsSpan * W);
+  uint32_t* prof = reinterpret_cast<uint32_t*>(smem);                                 // [mpad + 1][2]
+  uint32_t* sel = reinterpret_cast<uint32_t*>(smem + rs_prof_bytes(a.max_len)) + half * kRsSpan * W;
+  int32_t* s_best = reinterpret_cast<int32_t*>(smem + rs_prof_bytes(a.max_len) + 2 * (size_t)kRsSpan * W * 4);
 
   // profile rows k = 0..mpad: word q = 0 forward, q = 1 reverse complement
   for (int e = tid; e < (mpad + 1) * 2; e += kRsThreads) {
@@ -87,85 +95,110 @@ __global__ void __launch_bounds__(kRsThreads, 4) k_rescore_scan(RsArgs a) {
     }
     prof[e] = profile_word(code, a.prof_match, a.prof_mismatch);
   }
-  if (tid == 0) *s_best = 0;
+  if (tid < 2) s_best[tid] = 0;
   const uint32_t mmw = a.mm_word;
   const int ncols = (kRsTile + mpad + kRsD + kRsSpan - 1) / kRsSpan;
   const int ntile = (int)((a.F + kRsTile - 1) / kRsTile);
+  const int nfull = m / kRsD * kRsD, rem = m - nfull;
+  const int last_parity = (m - 1) & 1;
 
-  for (int c = 0; c < a.K; ++c) {
-    const int32_t f = a.cand[(int64_t)i * a.K + c];
-    if (f < 0) {
-      if (tid == 0) a.cand_max[(int64_t)i * a.K + c] = -1;
-      continue;
-    }
+  for (int c0 = 0; c0 < a.K; c0 += 2) {
+    // this half's candidate (the second half idles when K is odd)
+    const int c = c0 + half;
+    const int32_t f = c < a.K ? a.cand[(int64_t)i * a.K + c] : -1;
     for (int tt = 0; tt < ntile; ++tt) {
       const int64_t ts = (int64_t)f * a.F + (int64_t)tt * kRsTile;
       const int64_t lim = a.F - (int64_t)tt * kRsTile;  // pass positions p < lim are diagonals of f
       __syncthreads();  // the previous pass has finished reading the selectors
-      // selector column col: positions P = col*8 .. P+7 and their partners at +4 (12 codes)
-      for (int col = tid; col < ncols; col += kRsThreads) {
-        const int64_t q = ts + (int64_t)col * kRsSpan;
-        const int64_t w2 = q >> 4, wm = q >> 5;
-        const uint64_t gw = ((((uint64_t)a.g2[w2 + 1]) << 32) | a.g2[w2]) >> (2 * (int)(q & 15));
-        const uint64_t vw = ((((uint64_t)a.gm[wm + 1]) << 32) | a.gm[wm]) >> (int)(q & 31);
+      if (f >= 0) {
+        // selector column col: positions P = col*16 .. P+15 and their partners at +8, one byte
+        // per position (the 2-bit code, or the N code where the valid bit is 0), four
+        // positions per word built with carry-free multiplies
+        for (int col = ltid; col < ncols; col += kRsHalf) {
+          const int64_t q = ts + (int64_t)col * kRsSpan;
+          const int64_t w2 = q >> 4, wm = q >> 5;
+          const int sh = 2 * (int)(q & 15);
+          const uint32_t g0 = a.g2[w2], g1 = a.g2[w2 + 1], g2w = a.g2[w2 + 2];
+          const uint32_t lo = (uint32_t)(((((uint64_t)g1) << 32) | g0) >> sh);   // positions 0..15
+          const uint32_t hi = (uint32_t)(((((uint64_t)g2w) << 32) | g1) >> sh);  // positions 16..31
+          const uint32_t vw = (uint32_t)(((((uint64_t)a.gm[wm + 1]) << 32) | a.gm[wm]) >> (int)(q & 31));
+          uint32_t nb[3 * kRsD / 4];
 #pragma unroll
-        for (int r = 0; r < kRsSpan; ++r) {
-          const uint32_t c1 = ((vw >> r) & 1u) ? (uint32_t)((gw >> (2 * r)) & 3u) : 4u;
-          const uint32_t c2 = ((vw >> (r + kRsD)) & 1u) ? (uint32_t)((gw >> (2 * (r + kRsD))) & 3u) : 4u;
-          sel[r * W + col] = make_sel<F16>(c1, c2);
+          for (int k = 0; k < 3 * kRsD / 4; ++k) {
+            const uint32_t b = prmt(k < 4 ? lo : hi, 0u, 0x4440u | (uint32_t)(k & 3));
+            const uint32_t codes = ((((b * 4097u) & 0x000F000Fu) * 65u) & 0x03030303u);
+            const uint32_t vs = ((((vw >> (4 * k)) & 0xFu) * 0x00204081u) & 0x01010101u);
+            nb[k] = codes + (F16 ? 5u : 4u) * (0x01010101u - vs);
+          }
+#pragma unroll
+          for (int r = 0; r < kRsSpan; ++r) {
+            const uint32_t t2 =
+                prmt(nb[r >> 2], nb[(r + kRsD) >> 2], (uint32_t)(r & 3) | ((uint32_t)(4 + (r & 3)) << 4) | 0x8800u);
+            sel[r * W + col] = F16 ? t2 * 16u + 0x0404u : t2 * 17u + 0x8080u;
+          }
         }
       }
       __syncthreads();
+      if (f >= 0) {
+        uint32_t win[kRsD], H[2][kRsD], M[2][kRsD];
+#pragma unroll
+        for (int j = 0; j < kRsD; ++j) win[j] = sel[j * W + ltid];
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+#pragma unroll
+          for (int j = 0; j < kRsD; ++j) H[q][j] = 0u, M[q][j] = 0u;
+        uint2 pnext = reinterpret_cast<const uint2*>(prof)[0];
+        // blocks of 8 steps (pair j of step k0 + u reads win[(j + u) % 8]), the last one cut
+        // at the read's length
+        auto block = [&](int k0, auto tail, int nvalid) {
+          constexpr bool kTail = decltype(tail)::value;
+          const int kk = k0 + kRsD;
+          const uint32_t* sp = sel + (kk % kRsSpan) * W + ltid + kk / kRsSpan;
+          const uint2* pp = reinterpret_cast<const uint2*>(prof) + k0 + 1;
+#pragma unroll
+          for (int u = 0; u < kRsD; ++u) {
+            if (kTail && u >= nvalid) break;
+            const uint32_t pw[2] = {pnext.x, pnext.y};
+            pnext = pp[u];
+#pragma unroll
+            for (int q = 0; q < 2; ++q)
+#pragma unroll
+              for (int j = 0; j < kRsD; ++j) {
+                const uint32_t s = prmt(pw[q], mmw, win[(j + u) % kRsD]);
+                const uint32_t h = kadane_step<F16>(H[q][j], s);
+                if ((u & 1) != (j & 1)) M[q][j] = __vimax3_s16x2(M[q][j], H[q][j], h);
+                H[q][j] = h;
+              }
+            win[u] = sp[u * W];
+          }
+        };
+        for (int k0 = 0; k0 < nfull; k0 += kRsD) block(k0, BoolTagRs<false>{}, kRsD);
+        if (rem > 0) block(nfull, BoolTagRs<true>{}, rem);
+        // the pairs of the last step's parity hold one value not yet folded
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+#pragma unroll
+          for (int j = 0; j < kRsD; ++j)
+            if ((j & 1) == last_parity) M[q][j] = __vimax3_s16x2(M[q][j], H[q][j], 0u);
 
-      uint32_t win[kRsD], H[2][kRsD], M[2][kRsD];
+        // this thread's diagonals: pass positions ltid*16 + j (low lane) and + 8 + j (high lane)
+        const int p0 = ltid * kRsSpan;
+        uint32_t x = 0u;
 #pragma unroll
-      for (int j = 0; j < kRsD; ++j) win[j] = sel[j * W + tid];
-#pragma unroll
-      for (int q = 0; q < 2; ++q)
-#pragma unroll
-        for (int j = 0; j < kRsD; ++j) H[q][j] = 0u, M[q][j] = 0u;
-      uint2 pnext = reinterpret_cast<const uint2*>(prof)[0];
-      for (int k0 = 0; k0 < mpad; k0 += kRsD) {
-        const int kk = k0 + kRsD;
-        const uint32_t* sp = sel + (kk % kRsSpan) * W + tid + kk / kRsSpan;
-        const uint2* pp = reinterpret_cast<const uint2*>(prof) + k0 + 1;
-#pragma unroll
-        for (int u = 0; u < kRsD; ++u) {
-          const uint32_t pw[2] = {pnext.x, pnext.y};
-          pnext = pp[u];
-#pragma unroll
-          for (int q = 0; q < 2; ++q)
-#pragma unroll
-            for (int j = 0; j < kRsD; ++j) {
-              const uint32_t s = prmt(pw[q], mmw, win[(j + u) % kRsD]);
-              const uint32_t h = kadane_step<F16>(H[q][j], s);
-              if ((u & 1) != (j & 1)) M[q][j] = __vimax3_s16x2(M[q][j], H[q][j], h);
-              H[q][j] = h;
-            }
-          win[u] = sp[u * W];
+        for (int j = 0; j < kRsD; ++j) {
+          const uint32_t mask =
+              ((p0 + j < lim) ? 0x0000FFFFu : 0u) | ((p0 + kRsD + j < lim) ? 0xFFFF0000u : 0u);
+          x = __vimax3_s16x2(x, M[0][j] & mask, M[1][j] & mask);
         }
+        int32_t v = max(lane_value<F16>(x & 0xFFFFu), lane_value<F16>(x >> 16));
+        v = __reduce_max_sync(0xffffffffu, v);
+        if (lane == 0 && v > 0) atomicMax(&s_best[half], v);
       }
-#pragma unroll
-      for (int q = 0; q < 2; ++q)
-#pragma unroll
-        for (int j = 1; j < kRsD; j += 2) M[q][j] = __vimax3_s16x2(M[q][j], H[q][j], 0u);
-
-      // this thread's diagonals: pass positions tid*8 + j (low lane) and tid*8 + 4 + j (high lane)
-      const int p0 = tid * kRsSpan;
-      uint32_t x = 0u;
-#pragma unroll
-      for (int j = 0; j < kRsD; ++j) {
-        const uint32_t mask = ((p0 + j < lim) ? 0x0000FFFFu : 0u) | ((p0 + kRsD + j < lim) ? 0xFFFF0000u : 0u);
-        x = __vimax3_s16x2(x, M[0][j] & mask, M[1][j] & mask);
-      }
-      int32_t v = max(lane_value<F16>(x), lane_value<F16>(x >> 16));
-      v = __reduce_max_sync(0xffffffffu, v);
-      if (lane == 0 && v > 0) atomicMax(s_best, v);
     }
     __syncthreads();
-    if (tid == 0) {
-      a.cand_max[(int64_t)i * a.K + c] = *s_best;
-      *s_best = 0;  // the next candidate's first pass starts after a barrier
+    if (ltid == 0 && c < a.K) {
+      a.cand_max[(int64_t)i * a.K + c] = f >= 0 ? s_best[half] : -1;
+      s_best[half] = 0;  // the next pair's first pass starts after a barrier
     }
   }
 }
