@@ -155,6 +155,39 @@ def test_gradients_match_oracle(mss):
     prop.close()
 
 
+def test_first_layer_keeps_fp32_weights(mss):
+    """The first layer's weights are FP32 (the tensor-core kernel splits each into three
+    exact BF16 parts).  Two one-path channels: channel 0 reads base A through tap 3 with
+    weight 1 + 2^-9 + 2^-12 and bias 2^-9, whose exact sum 1 + 2^-8 + 2^-12 rounds to the BF16
+    value 1 + 2^-7, while a BF16 weight (1) plus the bias would round to 1; channel 1 reads
+    the same base with weight 1.  Layers 2-4 pass both channels on unchanged, so the
+    embedding's ratio e0 / e1 is 1 + 2^-7 exactly, as in the oracle."""
+    import torch
+    C, T = po.C, po.TAPS
+    p = np.zeros(po.param_count())
+    p[(3 * 4 + 0) * C + 0] = 1 + 2 ** -9 + 2 ** -12
+    p[(3 * 4 + 0) * C + 1] = 1.0
+    p[T * 4 * C + 0] = 2 ** -9
+    o = T * 4 * C + C
+    for _ in range(3):
+        p[o + (3 * C + 0) * C + 0] = 1.0
+        p[o + (3 * C + 1) * C + 1] = 1.0
+        o += T * C * C + C
+    codes = np.array([[1, 2, 3, 1, 2, 0, 3, 3, 1, 2, 1, 3]], dtype=np.uint8)   # one A, at 5
+    lens = np.array([12], dtype=np.int32)
+    want, _ = po.forward(p, codes[0])
+    assert want[0] / want[1] == 1 + 2 ** -7
+    prop = mss.Proposal(seed=2)
+    prop.set_params(p.astype(np.float32))
+    d_emb = torch.zeros(128, dtype=torch.float32, device="cuda")
+    prop.embed(dev(codes), dev(lens), 12, 1, 12, d_emb)
+    torch.cuda.synchronize()
+    got = d_emb.cpu().numpy().astype(np.float64)
+    prop.close()
+    assert np.abs(got - want).max() < 1e-6, (got[:3], want[:3])
+    assert got[0] / got[1] == pytest.approx(1 + 2 ** -7, abs=1e-6)
+
+
 def test_mean_pooling_matches_oracle(mss):
     """The mean-pooling option: embeddings (lengths 1 to 700, N bases, a sequence longer than
     a conv tile) against the oracle's mean pool with the same rounding points, the parameter
