@@ -172,9 +172,8 @@ __device__ void warp_emit(const uint32_t* key, const int32_t* frag, int n, int K
 }
 
 // The four epilogue warps of a read group (warps 4g .. 4g + 3 append to reads 16g .. 16g + 15
-// and compact them) synchronise on their own named barrier 2 + g; the "or" form also makes
-// every warp of the group take the same abort decision.
-__device__ __forceinline__ void grp_bar(int g) { asm volatile("bar.sync %0, 128;" ::"r"(2 + g) : "memory"); }
+// and compact them) synchronise on their own named barrier 2 + g; the "or" form makes every
+// warp of the group take the same decision (abort, or reload the thresholds).
 __device__ __forceinline__ bool grp_bar_or(int g, bool p) {
   uint32_t r;
   asm volatile(
