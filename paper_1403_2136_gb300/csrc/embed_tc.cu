@@ -44,7 +44,9 @@ constexpr uint32_t kL1BytesA = kPropC * kL1Parts * kL1KPart * 2;  // 24,576
 constexpr uint32_t kL1BytesB = kL1M * kL1KPart * 2;               // 8,192
 constexpr int kL1Stages = 2;
 constexpr uint32_t kL1OffB = kL1BytesA;
-constexpr uint32_t kL1OffBar = kL1OffB + kL1Stages * kL1BytesB;
+constexpr int kL1Codes = 160;                        // codes of positions p0 - 3 .. p0 + 132 (136 used)
+constexpr uint32_t kL1OffCodes = kL1OffB + kL1Stages * kL1BytesB;
+constexpr uint32_t kL1OffBar = kL1OffCodes + kL1Stages * kL1Codes;
 // at most two CTAs per SM, whose accumulators (256 columns each) fill the tensor memory
 constexpr uint32_t kL1Smem = 80 * 1024;
 static_assert(kL1OffBar + 128 <= kL1Smem, "shared memory of the first-layer CTA");
@@ -106,7 +108,7 @@ __global__ void __launch_bounds__(kL1Threads, 1)
   const uint32_t tmem = s_tmem;
   const uint32_t sA = smem_u32(sm), sB = sA + kL1OffB;
 
-  if (warp == 0) {  // B builder: lane = (position p, 4 K-chunks), 16 chunks per lane
+  if (warp == 0) {  // B builder: the item's codes into shared memory, then 16 chunks per lane
     bool ok = true;
     for (int k = 0; k < count && count > 0; ++k) {
       const int s = k % kL1Stages, u = k / kL1Stages;
@@ -117,15 +119,24 @@ __global__ void __launch_bounds__(kL1Threads, 1)
       const int n = j / ntile, p0 = (j - n * ntile) * kL1M;
       const int len = lens[n];
       if (ok && p0 < len) {
+        // cb[e] = code of position p0 - 3 + e (4 outside the sequence): one batch of loads
         const uint8_t* cn = codes + (int64_t)n * ld;
+        uint8_t* cb = sm + kL1OffCodes + s * kL1Codes;
+#pragma unroll
+        for (int e = lane; e < kL1Codes; e += 32) {
+          const int q = p0 - 3 + e;
+          cb[e] = (e < kL1M + 8 && q >= 0 && q < len) ? cn[q] : (uint8_t)4;
+        }
+        __syncwarp();
         uint8_t* dst = sm + kL1OffB + s * kL1BytesB;
+#pragma unroll 4
         for (int e = lane; e < kL1M * (kL1KPart / 8); e += 32) {
           const int p = e >> 2, g = e & 3;  // chunk g: taps 2g and 2g + 1 (tap 7 is padding)
           uint32_t w[4];
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
-            const int t = 2 * g + h, q = p0 + p + t - 3;
-            const uint32_t c = (t < kPropTaps && q >= 0 && q < len) ? (uint32_t)cn[q] : 4u;
+            const int t = 2 * g + h;
+            const uint32_t c = t < kPropTaps ? (uint32_t)cb[p + t] : 4u;
             // four BF16 indicators of bases 0..3: 1.0 = 0x3F80
             w[2 * h] = (c == 0u ? 0x3F80u : 0u) | (c == 1u ? 0x3F800000u : 0u);
             w[2 * h + 1] = (c == 2u ? 0x3F80u : 0u) | (c == 3u ? 0x3F800000u : 0u);
