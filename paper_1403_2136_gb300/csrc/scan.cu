@@ -539,7 +539,7 @@ cudaError_t launch_scan(const ScanConfig& c, const ScanArgs& a, int grid, size_t
 // with plain int32 arithmetic to find the best diagonal (ties: + strand first, then smallest
 // d).  The rescan costs 2*F*m cells per read (1/NF of the scan).
 constexpr int kFinWarps = 4;
-constexpr int kFinChunk = 1024;  // diagonals staged per pass
+constexpr int kFinChunk = 512;   // diagonals staged per pass (and the granularity of the early stop)
 
 __global__ void __launch_bounds__(kFinWarps * 32) k_finalize(FinalArgs a) {
   __shared__ uint8_t s_gen[kFinWarps][kFinChunk + MSS_MAX_READ_LEN + 16];
@@ -593,8 +593,13 @@ __global__ void __launch_bounds__(kFinWarps * 32) k_finalize(FinalArgs a) {
   int32_t bestK = -1, bestS = 0;
   int64_t bestD = 0;
   const int64_t d_lo = (int64_t)f1 * a.F, d_hi = d_lo + a.F;
-  for (int sg = 0; sg < 2; ++sg) {
-    for (int64_t d0 = d_lo; d0 < d_hi; d0 += kFinChunk) {
+  // (strand, d) in increasing order, chunk by chunk: the answer is the first pair whose score
+  // is the fragment's score, so the rescan stops after the first chunk in which some lane
+  // reached it (every earlier chunk scored less); without such a chunk it runs to the end and
+  // the self-check below reports the mismatch
+  bool found = false;
+  for (int sg = 0; sg < 2 && !found; ++sg) {
+    for (int64_t d0 = d_lo; d0 < d_hi && !found; d0 += kFinChunk) {
       const int64_t nd = (d_hi - d0 < (int64_t)kFinChunk) ? d_hi - d0 : (int64_t)kFinChunk;
       __syncwarp();
       for (int64_t i = lane; i < nd + m; i += 32) s_gen[wib][i] = (uint8_t)genome_code(a.g2, a.gm, d0 + i);
@@ -623,6 +628,7 @@ __global__ void __launch_bounds__(kFinWarps * 32) k_finalize(FinalArgs a) {
           bestD = d0 + i;
         }
       }
+      found = __any_sync(0xffffffffu, bestK == acc.s1);
     }
   }
   // warp argmax: larger K, then smaller strand, then smaller d
