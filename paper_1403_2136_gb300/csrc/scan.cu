@@ -254,32 +254,46 @@ __global__ void __launch_bounds__(NT, MINB) k_scan(ScanArgs a) {
         const uint32_t* rg2 = reinterpret_cast<const uint32_t*>(raw + buf * Geo::kRawBytes);
         const uint32_t* rgm = reinterpret_cast<const uint32_t*>(raw + buf * Geo::kRawBytes + Geo::kRawG2Bytes);
         // one selector column per thread: positions P .. P + SPAN - 1 and their partners at
-        // +D; their 2-bit codes and valid bits fit in two aligned words each
-        const int ncols = (TILE + STEP * mpad + D + SPAN - 1) / SPAN;
-        for (int col = tid; col < ncols; col += NT) {
-          const int P = col * SPAN;
-          const uint64_t gw = ((((uint64_t)rg2[(P >> 4) + 1]) << 32) | rg2[P >> 4]) >> (2 * (P & 15));
-          const uint32_t vw = (uint32_t)(((((uint64_t)rgm[(P >> 5) + 1]) << 32) | rgm[P >> 5]) >> (P & 31));
-          // one byte per position, n = the 2-bit code, or the N code where the valid bit is 0
-          // (packed N and padding carry code 0), four positions per word, built with
-          // carry-free multiplies: bytes of 4 codes -> 2-bit fields 8 bits apart; 4 valid
-          // bits -> bit 0 of 4 bytes
+        // +D; their 2-bit codes and valid bits fit in two aligned words each.  One byte per
+        // position, n = the 2-bit code, or the N code where the valid bit is 0 (packed N and
+        // padding carry code 0), four positions per word, built with carry-free multiplies:
+        // bytes of 4 codes -> 2-bit fields 8 bits apart; 4 valid bits -> bit 0 of 4 bytes
+        auto nbytes = [&](uint64_t gw, uint32_t vw, int k) {
+          const uint32_t b = prmt(k < 4 ? (uint32_t)gw : (uint32_t)(gw >> 32), 0u, 0x4440u | (uint32_t)(k & 3));
+          const uint32_t codes = ((((b * 4097u) & 0x000F000Fu) * 65u) & 0x03030303u);
+          const uint32_t vs = ((((vw >> (4 * k)) & 0xFu) * 0x00204081u) & 0x01010101u);
+          return codes + (F16 ? 5u : 4u) * (0x01010101u - vs);
+        };
+        auto window = [&](int P, uint64_t& gw, uint32_t& vw) {
+          gw = ((((uint64_t)rg2[(P >> 4) + 1]) << 32) | rg2[P >> 4]) >> (2 * (P & 15));
+          vw = (uint32_t)(((((uint64_t)rgm[(P >> 5) + 1]) << 32) | rgm[P >> 5]) >> (P & 31));
+        };
+        // bytes [n(P + r), n(P + r + D), 0, 0] (the zero bytes replicate the sign of a byte
+        // <= 5), then the selector word of make_sel with one multiply-add
+        auto selector = [&](uint32_t na, uint32_t nbw, int r) {
+          const uint32_t t2 = prmt(na, nbw, (uint32_t)(r & 3) | ((uint32_t)(4 + (r & 3)) << 4) | 0x8800u);
+          return F16 ? t2 * 16u + 0x0404u : t2 * 17u + 0x8080u;
+        };
+        {
+          const int col = tid;  // the tile's own columns: one per thread
+          uint64_t gw;
+          uint32_t vw;
+          window(col * SPAN, gw, vw);
           uint32_t nb[3 * D / 4];
 #pragma unroll
-          for (int k = 0; k < 3 * D / 4; ++k) {
-            const uint32_t b = prmt(k < 4 ? (uint32_t)gw : (uint32_t)(gw >> 32), 0u, 0x4440u | (uint32_t)(k & 3));
-            const uint32_t codes = ((((b * 4097u) & 0x000F000Fu) * 65u) & 0x03030303u);
-            const uint32_t vs = ((((vw >> (4 * k)) & 0xFu) * 0x00204081u) & 0x01010101u);
-            nb[k] = codes + (F16 ? 5u : 4u) * (0x01010101u - vs);
-          }
+          for (int k = 0; k < 3 * D / 4; ++k) nb[k] = nbytes(gw, vw, k);
 #pragma unroll
-          for (int r = 0; r < SPAN; ++r) {
-            // bytes [n(P + r), n(P + r + D), 0, 0] (the zero bytes replicate the sign of a byte
-            // <= 5), then the selector word of make_sel with one multiply-add
-            const uint32_t t2 =
-                prmt(nb[r >> 2], nb[(r + D) >> 2], (uint32_t)(r & 3) | ((uint32_t)(4 + (r & 3)) << 4) | 0x8800u);
-            sel[r * W + col] = F16 ? t2 * 16u + 0x0404u : t2 * 17u + 0x8080u;
-          }
+          for (int r = 0; r < SPAN; ++r) sel[r * W + col] = selector(nb[r >> 2], nb[(r + D) >> 2], r);
+        }
+        // the columns past the tile (the window's overhang) selector by selector, spread over
+        // the threads, so that no thread builds two whole columns
+        const int ncols = (TILE + STEP * mpad + D + SPAN - 1) / SPAN;
+        for (int e = tid; e < (ncols - NT) * SPAN; e += NT) {
+          const int col = NT + e / SPAN, r = e % SPAN;
+          uint64_t gw;
+          uint32_t vw;
+          window(col * SPAN, gw, vw);
+          sel[r * W + col] = selector(nbytes(gw, vw, r >> 2), nbytes(gw, vw, (r + D) >> 2), r);
         }
       }
       __syncthreads();
