@@ -13,7 +13,9 @@
 // maximum, and append every score above the read's current threshold to the read's candidate
 // buffer in shared memory (one warp vote per tile, then a ballot + one shared atomic per read
 // that has a passing score).  When a buffer passes 128 entries the epilogue warps keep
-// its K best (warp-wide selection of the K-th largest key) and raise the threshold.  Tiles
+// its K best (warp-wide selection of the K-th largest key) and raise the threshold.  The
+// four warps of a group of 16 reads synchronise among themselves only (named barriers) and
+// keep the group's thresholds in registers, reloading them after a tile that raised one.  Tiles
 // are processed in increasing fragment order, so a later fragment equal to the threshold
 // loses the tie and is never appended.  With several CTAs per read block (fragment splits)
 // every split writes its K best and k_topk_merge keeps the K best of the splits.
