@@ -60,3 +60,12 @@ def test_null_context_is_rejected_without_a_gpu(lib):
     # argument checks happen before any CUDA call
     assert lib.mss_get_info(None, None) == -1
     assert lib.mss_last_error()
+
+
+def test_null_proposal_model_is_rejected_without_a_gpu(lib):
+    import paper_1403_2136_gb300 as mss
+    # argument checks of the proposal entry points happen before any CUDA call
+    assert lib.mss_prop_set_pooling(None, 1) == mss.MSS_EINVAL
+    assert lib.mss_prop_get_pooling(None) == -1
+    assert lib.mss_prop_launch_count(None) == -1
+    assert lib.mss_prop_save(None, b"/nonexistent") == mss.MSS_EINVAL
