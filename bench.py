@@ -100,7 +100,7 @@ def batches(seq, off, batch: int):
 # 50,000-read batch, F = 2048, read step 1), from an ncu capture of that launch with
 # dram__bytes_read.sum and dram__bytes_write.sum (one pass; the command and the figures are in
 # profiles/launches_bact-4.6M_50k-read-batch.md).  Other workloads report no traffic.
-SCAN_DRAM_BYTES_DEFAULT = 8.884992e6
+SCAN_DRAM_BYTES_DEFAULT = 9.018112e6
 
 
 def workload_config(wl, genome, lengths, F: int, args, world: int = 1) -> dict:
